@@ -1,0 +1,360 @@
+#!/usr/bin/env python3
+"""Benchmark of the ghost-point IBM / ADE / LEE hot path on B300.
+
+Default workload: the batched cylinder-pulse sweep -- 512 independent solves,
+grid n^2 with n uniform in {256, 384, 512, 768, 1024}, cylinder radius 0.1 n,
+R, M, K log-uniform in [0.2, 5] x [0.005, 0.2] x [0.5, 20] (seed 24785), FP32
+field storage and stencils with FP64 ghost weights / ADE, advanced together by
+one ghost launch and one stencil launch per Runge-Kutta stage (CUDA graph).
+A step is one time step (four stages) of every instance.  Metric: point-stage
+updates per second (fluid nodes x 4 stages x steps / time).  The device
+working set (~10 GB) is far larger than L2, so no flush is needed.
+
+--workload cylinder times the single 1024^2 cylinder-pulse solve instead.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (the reference arm).
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpoint-stage-updates/s"
+UNIT = "Mpoint-stage/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lee", choices=["lee", "reference"])
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "cylinder"])
+    ap.add_argument("--count", type=int, default=512)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def workload_cases(args, rank, accept=None):
+    from paper_2609_24785_b300 import workloads
+    if args.workload == "sweep":
+        cases, rejected = workloads.sweep(args.count, seed=24785 + rank, accept=accept)
+        desc = ("batched cylinder-pulse sweep: %d instances, n^2 with n in {256,384,512,768,1024}, "
+                "cylinder r = 0.1 n, R/M/K log-uniform, seed %d" % (args.count, 24785 + rank))
+        return cases, rejected, desc
+    c = workloads.cylinder_pulse(1024)
+    return [c], 0, "cylinder pulse 1024^2, r = 50 cells, R=2 M=0.02 K=1"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(device_index)],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(case, target_seconds=15.0):
+    """The FP64 oracle as it stands, on one instance of the workload, on all host
+    cores (OpenMP); runs a bounded number of steps."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from _helpers import make_oracle
+    o = make_oracle(case)
+    fluid = int((o.kind() == 1).sum())
+    t = time.perf_counter()
+    o.run(2)
+    dt1 = (time.perf_counter() - t) / 2
+    n = max(2, min(2000, int(target_seconds / max(dt1, 1e-6))))
+    t = time.perf_counter()
+    o.run(n)
+    el = time.perf_counter() - t
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": fluid * 4 * n / el / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%s (%d fluid nodes), %d steps, %.1f s" % (case.name, fluid, n, el)}
+
+
+def run_reference(args):
+    ws, rank, local = dist_setup(args)
+    if rank != 0:
+        return
+    from paper_2609_24785_b300 import workloads
+    cases, _, desc = workload_cases(args, 0)
+    case = min(cases, key=lambda c: c.points) if args.workload == "sweep" else workloads.cylinder_pulse(256)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from _helpers import make_oracle
+    o = make_oracle(case)
+    fluid = int((o.kind() == 1).sum())
+    for _ in range(args.warmup):
+        o.run(1)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        o.run(1)
+    el = time.perf_counter() - t
+    v = fluid * 4 * args.steps / el / 1e6
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = "%s (%d fluid nodes), one time step per bench step" % (case.name, fluid)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_lee(args):
+    import torch
+    ws, rank, local = dist_setup(args)
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_2609_24785_b300 import lee, workloads
+    lee.load()
+
+    def accept(case):
+        s = lee.Solver(case.nx, case.ny, case.h, case.cfl, precision=args.precision)
+        workloads.apply_to(case, s)
+        try:
+            s.plan()
+            return True
+        except lee.LeeError as e:
+            if e.code == lee.LEE_ERR_ADE_UNSTABLE:
+                return False
+            raise
+
+    t_setup = time.perf_counter()
+    cases, rejected, desc = workload_cases(args, rank, accept=accept)
+    stream = torch.cuda.Stream(device=dev)
+    batch = lee.Batch(args.precision, stream=stream)
+    solvers = []
+    from concurrent.futures import ThreadPoolExecutor
+
+    def plan(case):
+        s = lee.Solver(case.nx, case.ny, case.h, case.cfl, precision=args.precision)
+        workloads.apply_to(case, s)
+        if len(case.probes):
+            s.set_probes(case.probes, 4096)
+        s.plan()
+        return s
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        solvers = list(ex.map(plan, cases))
+    for case, s in zip(cases, solvers):
+        s.bind(stream=stream)
+        workloads.apply_state(case, s)
+        batch.add(s)
+    t_setup = time.perf_counter() - t_setup
+    fluid = sum(s.sizes.n_fluid for s in solvers)
+    ghosts = sum(s.sizes.n_ghost for s in solvers)
+    elem = 4 if args.precision == "fp32" else 8
+
+    # warm-up (also captures the CUDA graphs)
+    batch.step(args.warmup)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---- timed region: K steps of every instance, device time by CUDA events
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    l0 = lee.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    batch.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = lee.launch_count() - l0
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        f = torch.tensor([float(fluid)], device=dev)
+        dist.all_reduce(f)
+        fluid_all = float(f.item())
+    else:
+        fluid_all = float(fluid)
+    value = fluid_all * 4 * args.steps / (ms / 1e3) / 1e6
+
+    # ---- roofline of the dominant kernel (stencil, stage 2: reads Q(1) and
+    # Q^n, writes Q(2): 9 words per fluid node), timed on the launching stream
+    reps = 10
+    for _ in range(2):
+        batch.launch(2, 1)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(reps):
+        batch.launch(2, 1)
+    a1.record(stream)
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(reps):
+        batch.launch(2, 0)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    st_ms = a0.elapsed_time(a1) / reps
+    gh_ms = g0.elapsed_time(g1) / reps
+    alg_bytes = 9 * elem * fluid
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (st_ms / 1e3) / 1e9
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "stencil_traffic.json")
+    if os.path.exists(tf):
+        try:
+            d = json.load(open(tf))
+            if d.get("workload") == desc and d.get("precision") == args.precision:
+                traffic = d.get("bytes_per_launch")
+        except (ValueError, OSError):
+            traffic = None
+
+    # ---- end to end through the C ABI with host buffers: every step uploads
+    # every instance's state from pinned host memory, advances one step and
+    # reads back the step's probe record
+    e2e = None
+    if not args.no_e2e:
+        import ctypes as C
+        blobs = [torch.from_numpy(s.read_state()).pin_memory() for s in solvers]
+        pr = [torch.empty(max(s._nprobe, 1), dtype=torch.float64).pin_memory() for s in solvers]
+        recs = [int(np.frombuffer(b.numpy()[:16].tobytes(), dtype=np.int64)[1]) for b in blobs]
+        h2d = sum(b.numel() for b in blobs)
+        d2h = sum(8 * s._nprobe for s in solvers)
+        L = lee.load()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for it in range(args.steps):
+            for s, b in zip(solvers, blobs):
+                lee._check(L.lee_upload_state_async(s.ctx, C.c_void_p(b.data_ptr())), s.ctx)
+            batch.step(1)
+            for s, p, r in zip(solvers, pr, recs):
+                if s._nprobe and r < 4096:
+                    rec = r   # the uploaded state carries the record count; this step writes record r
+                    lee._check(L.lee_download_probes_async(s.ctx, C.cast(C.c_void_p(p.data_ptr()), lee._dp), rec, 1), s.ctx)
+            stream.synchronize()
+        el = time.perf_counter() - t0
+        barrier()
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([el], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": fluid_all * 4 * args.steps / el / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "what": "per step: state of every instance H2D from pinned host memory, one step, probe record D2H"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        small = min(cases, key=lambda c: c.points)
+        cpu = cpu_baseline(small)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": desc, "instances": len(cases), "rejected_unstable_draws": rejected,
+                       "fluid_nodes": int(fluid), "ghost_points": int(ghosts),
+                       "ghost_dtype": "f64", "l2": "working set %.1f GB >> 126 MB L2, no flush" %
+                       (sum(s.sizes.device_bytes for s in solvers) / 1e9),
+                       "parallelism": "replicas" if ws > 1 else "single GPU", "setup_s": round(t_setup, 2)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "stencil_kernel<%s> stage 2" % ("float" if elem == 4 else "double"),
+                         "launch_ms": st_ms, "alg_bytes_per_launch": int(alg_bytes),
+                         "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind},
+            "ghost_kernel_ms": gh_ms,
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_lee(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,220 @@
+/*
+ * lee.h -- C ABI of the B300 ghost-point IBM / ADE impedance / 2D linearized
+ * Euler solver (liblee.so).
+ *
+ * The library computes the method of "A high-order ghost-point immersed
+ * boundary method coupled with auxiliary differential equations for
+ * time-domain impedance walls": one 2N-storage Runge-Kutta stage of the LEE
+ * (Sec. 2.1 Eq. 1, Sec. 2.2 Eq. DRP_s) coupled to the normal-stencil ghost
+ * points (Sec. 3.1, Eqs. ns-rotation .. ns-ghost) and the mass-spring-damper
+ * ADE (Sec. 2.5), with the six coupling steps of Sec. 3.2 at every stage.
+ *
+ * Conventions used by every entry point
+ *  - Grid: nx x ny nodes, node (i, j) at x = x0 + i h, y = y0 + j h; c0 = rho0 = 1,
+ *    dt = cfl * h.  Lengths and times are physical (same unit as h), so the
+ *    impedance R, M, K is in units of rho0 c0 with that length unit.
+ *  - Status: every function returns LEE_OK (0) or one of LEE_ERR_*; after an
+ *    error lee_last_error() returns a message.  No entry point aborts.
+ *  - Memory: the library never allocates device memory.  lee_plan() reports
+ *    the device bytes it needs; the caller allocates them (PyTorch in the
+ *    Python binding) and passes the pointer to lee_bind().  Host arrays passed
+ *    in are copied before the call returns (caller keeps ownership); host
+ *    output buffers are caller-owned and must hold the documented number of
+ *    elements.
+ *  - Streams: all device work is enqueued on the stream given to lee_bind();
+ *    entry points that return host data synchronise that stream.
+ *  - Thread safety: a context is used by one host thread at a time.
+ */
+#ifndef LEE_H
+#define LEE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define LEE_OK               0
+#define LEE_ERR_ARG          1  /* bad argument or call order                        */
+#define LEE_ERR_GEOMETRY     2  /* wall geometry not representable on this grid      */
+#define LEE_ERR_RANK         3  /* an elliptical cloud is rank deficient at degree 1 */
+#define LEE_ERR_ADE_UNSTABLE 4  /* an admittance pole lies outside the RK4 region    */
+#define LEE_ERR_BUDGET       5  /* device buffer too small / over budget             */
+#define LEE_ERR_CUDA         6  /* a CUDA call failed (message has the CUDA error)   */
+#define LEE_ERR_DIVERGED     7  /* field is no longer finite                         */
+#define LEE_ERR_TIMEOUT      8  /* a bounded device wait gave up                     */
+
+/* bulk field precision (ghost weights, ghost projections and ADE are FP64 always) */
+#define LEE_FP64 0
+#define LEE_FP32 1
+
+/* outer boundary treatment per axis */
+#define LEE_BC_RADIATION 0      /* one-sided stencils + radiation condition in 3 layers */
+#define LEE_BC_PERIODIC  1
+
+/* field selectors */
+#define LEE_P 0
+#define LEE_U 1
+#define LEE_V 2
+
+typedef struct lee_ctx lee_ctx;
+typedef struct lee_batch lee_batch;
+
+typedef struct {
+    int nx, ny;            /* nodes per axis, >= 8 (radiation) or >= 7 (periodic)  */
+    double h;              /* grid spacing, > 0                                    */
+    double cfl;            /* dt = cfl * h (c0 = 1), 0 < cfl                        */
+    double x0, y0;         /* coordinates of node (0, 0)                            */
+    int precision;         /* LEE_FP64 or LEE_FP32                                  */
+    int bc_x, bc_y;        /* LEE_BC_RADIATION or LEE_BC_PERIODIC                   */
+} lee_grid;
+
+typedef struct {
+    long long device_bytes;   /* bytes of device memory lee_bind() needs (256-B aligned) */
+    int n_ghost;              /* ghost points (Sec. 3.1)                                 */
+    int n_fluid;              /* fluid nodes advanced per stage                          */
+    long long n_entries;      /* total cloud entries over all ghosts                     */
+    int n_reduced;            /* ghosts whose LSQ degree was lowered below k = 4         */
+    int regime;               /* 0 rigid, 1 complex pair, 2 real poles, 3 double pole    */
+    double dt;                /* time step                                               */
+    double ade_amplification; /* max |P(pole dt)| of the RK4 polynomial over the poles  */
+    int n_tiles;              /* stencil tiles                                           */
+} lee_sizes;
+
+/* ---- context life cycle ------------------------------------------------- */
+/* Create a context for one solve on grid g.  *out receives the handle. */
+int lee_create(lee_ctx **out, const lee_grid *g);
+/* Destroy a context (does not free the caller's device buffer). */
+int lee_destroy(lee_ctx *ctx);
+/* Message of the last error on ctx (or of the last lee_create failure if ctx is NULL). */
+const char *lee_last_error(const lee_ctx *ctx);
+
+/* ---- geometry and impedance (before lee_plan) -------------------------- */
+/* No immersed wall: every node is fluid. */
+int lee_set_wall_none(lee_ctx *ctx);
+/* Straight wall through (xw, yw) at angle `angle` (radians) to the x-axis; the
+ * wall normal n = (-sin angle, cos angle) points into the fluid, i.e. node x is
+ * fluid when (x - xw) . n > 0 (Sec. 4.1, App. A). */
+int lee_set_wall_line(lee_ctx *ctx, double xw, double yw, double angle);
+/* Circular cylinder of radius r (> 3.5 h) centred at (xc, yc): nodes with
+ * |x - c| > r are fluid (Sec. 4.2). */
+int lee_set_wall_cylinder(lee_ctx *ctx, double xc, double yc, double r);
+/* Mass-spring-damper wall Z(s) = M s + R + K/s, M, R, K > 0 (Sec. 2.5).  The
+ * three pole regimes (complex pair, two real poles, double pole at
+ * R = 2 sqrt(KM)) are all supported. */
+int lee_set_impedance(lee_ctx *ctx, double R, double M, double K);
+/* Rigid wall, the limit Y -> 0: u_n = 0 and dp/dn = 0 (Sec. 2.4). */
+int lee_set_rigid(lee_ctx *ctx);
+
+/* ---- plan and bind ------------------------------------------------------ */
+/* Host set-up (Sec. 3.1): mask, ghost set, boundary points, elliptical clouds,
+ * FP64 Householder-QR least squares, Lagrange factors, combined weight rows;
+ * ADE poles/residues (Sec. 2.5) and the RK4 stability check of the poles.
+ * Fills *out.  Returns LEE_ERR_ADE_UNSTABLE if a pole times dt lies outside
+ * the RK4 stability region, LEE_ERR_RANK / LEE_ERR_GEOMETRY on bad geometry.
+ * Probes (lee_set_probes) must be set before lee_plan. */
+int lee_plan(lee_ctx *ctx, lee_sizes *out);
+/* Attach caller-owned device memory (dev_ptr, 256-byte aligned, dev_bytes >=
+ * sizes.device_bytes) and a cudaStream_t (passed as void*, NULL = legacy
+ * default stream).  Uploads the tables, zeroes the fields and ADE state. */
+int lee_bind(lee_ctx *ctx, void *dev_ptr, long long dev_bytes, void *stream);
+
+/* ---- initial state and source ------------------------------------------- */
+/* Gaussian pulse p = amp exp(-ln2 |x - xs|^2 / w^2), u = v = 0 at fluid nodes
+ * (Sec. 4.2); resets ADE states, step counter and probe records. */
+int lee_init_pulse(lee_ctx *ctx, double xs, double ys, double amp, double halfwidth);
+/* Wave packet of Sec. 4.1 along direction `angle`: s = (x - xs).d,
+ * p = amp/2 exp(-alpha^2 s^2) cos(2 pi k s), (u, v) = p d; resets as above. */
+int lee_init_packet(lee_ctx *ctx, double xs, double ys, double angle, double amp, double k, double alpha);
+/* Harmonic monopole s = amp exp(-ln2 |x - xs|^2 / w^2) sin(omega t) (Sec. 4.3).
+ * The time factor enters each stage as its moment over the step, which keeps
+ * the four-stage scheme 4th order.  amp = 0 removes the source.  May be called
+ * before or after lee_bind. */
+int lee_set_monopole(lee_ctx *ctx, double xs, double ys, double amp, double halfwidth, double omega);
+/* Overwrite one field (LEE_P/U/V) from a host array of nx*ny doubles (row-major,
+ * j slowest).  Values at non-fluid nodes are ignored. */
+int lee_write_field(lee_ctx *ctx, int which, const double *host);
+
+/* ---- probes --------------------------------------------------------------- */
+/* n pressure probes at (xy[2i], xy[2i+1]), recorded after every step into a
+ * device history of `capacity` records (4x4 Lagrange interpolation of degree 3
+ * when all 16 nodes are fluid, else the nearest fluid node).  Before lee_plan. */
+int lee_set_probes(lee_ctx *ctx, int n, const double *xy, int capacity);
+/* Copy the recorded probe history (records x n doubles) to host; *nrec gets the
+ * number of records (<= capacity). */
+int lee_read_probes(lee_ctx *ctx, double *host, long long *nrec);
+
+/* ---- time stepping ------------------------------------------------------- */
+/* Advance nsteps time steps (4 stages each) on the bound stream; asynchronous.
+ * Each stage runs the ghost/ADE kernel (steps 1-5 of Sec. 3.2) and the fused
+ * stencil + stage-update kernel (step 6).  The first call captures one step in
+ * a CUDA graph that later calls replay. */
+int lee_step(lee_ctx *ctx, long long nsteps);
+/* Wait for the bound stream. */
+int lee_sync(lee_ctx *ctx);
+
+/* ---- read back ------------------------------------------------------------ */
+/* Field LEE_P/U/V of Q^n as nx*ny doubles (FP32 storage is widened). */
+int lee_read_field(lee_ctx *ctx, int which, double *host);
+/* Node kinds, nx*ny bytes: 0 solid, 1 fluid, 2 ghost. */
+int lee_read_mask(lee_ctx *ctx, unsigned char *host);
+/* ADE states X^n, n_ghost x 2 doubles, in the ghost order of lee_ghost_info. */
+int lee_read_ade(lee_ctx *ctx, double *host);
+/* Completed time steps. */
+int lee_get_step(lee_ctx *ctx, long long *steps);
+/* Acoustic energy 1/2 h^2 sum_fluid (p^2 + u^2 + v^2) of Q^n (FP64 sum). */
+int lee_energy(lee_ctx *ctx, double *out);
+
+/* ---- checkpoint ----------------------------------------------------------- */
+/* Bytes of a state blob: Q^n at fluid nodes, ADE states, step counter, probes. */
+int lee_state_bytes(lee_ctx *ctx, long long *bytes);
+int lee_read_state(lee_ctx *ctx, void *host_blob);
+int lee_write_state(lee_ctx *ctx, const void *host_blob);
+
+/* Asynchronous variants for streaming use (no synchronisation; the host
+ * memory must stay valid until the bound stream has passed the copy; use
+ * page-locked memory for overlap).  The blob layout is lee_read_state's. */
+int lee_upload_state_async(lee_ctx *ctx, const void *host_blob);
+/* Copy probe records [first, first + count) to host asynchronously. */
+int lee_download_probes_async(lee_ctx *ctx, double *host, long long first, long long count);
+
+/* ---- test hooks ----------------------------------------------------------- */
+/* Ghost g of the plan: target node index (j*nx + i), boundary point, normal,
+ * r = d/h, degree m, cloud size. meta = {bpx, bpy, nx, ny, r}. */
+int lee_ghost_info(lee_ctx *ctx, int g, int *target, double *meta, int *m, int *ncloud);
+/* Cloud of ghost g: node indices and the combined FP64 weight rows
+ * w[4*e + {0,1,2,3}] = {L0, w_p, w_d, w_f}; kappa = {kappa_p, kappa_u} such that
+ * p_g = w_p.p + kappa_p dp/dn, w_g = w_d.(u.n) + kappa_u w_BP, t_g = w_f.(u.tau),
+ * p_BP = L0.p. */
+int lee_ghost_weights(lee_ctx *ctx, int g, int *idx, double *w, double *kappa);
+
+/* ---- batches: many instances per launch ---------------------------------- */
+/* A batch advances several bound contexts (any sizes, precisions must match)
+ * with one ghost launch and one stencil launch per stage over all of them. */
+int lee_batch_create(lee_batch **out, int precision);
+int lee_batch_destroy(lee_batch *b);
+/* Add a bound context; the batch uses the context's own device buffers. */
+int lee_batch_add(lee_batch *b, lee_ctx *ctx);
+/* Remove a context (at a step boundary). */
+int lee_batch_remove(lee_batch *b, lee_ctx *ctx);
+/* Device bytes the batch tables need for its current members. */
+int lee_batch_plan(lee_batch *b, long long *device_bytes);
+/* Attach caller-owned device memory for the batch tables and a stream. */
+int lee_batch_bind(lee_batch *b, void *dev_ptr, long long dev_bytes, void *stream);
+/* Advance every member nsteps steps. */
+int lee_batch_step(lee_batch *b, long long nsteps);
+const char *lee_batch_last_error(const lee_batch *b);
+/* Measurement hook: enqueue only one kernel of stage `stage` (1..4) for every
+ * member: what = 0 ghost/ADE kernel, 1 stencil kernel.  Stages 2..4 read and
+ * write disjoint buffers, so repeated launches are idempotent. */
+int lee_batch_launch(lee_batch *b, int stage, int what);
+
+/* ---- library --------------------------------------------------------------- */
+/* Kernel launches enqueued by this process so far (all contexts and batches). */
+long long lee_launch_count(void);
+/* Version string. */
+const char *lee_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LEE_H */

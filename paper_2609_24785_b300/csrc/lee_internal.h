@@ -1,0 +1,127 @@
+// lee_internal.h -- structures shared by the host set-up, the C ABI and the
+// CUDA kernels of liblee.  Not part of the public interface (include/lee.h).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace lee {
+
+// Tile of the fused stencil kernel: TILE_X columns x TILE_Y rows of outputs.
+constexpr int TILE_X = 64;
+constexpr int TILE_Y = 32;
+constexpr int HALO = 4;                 // smem halo on each side (7-pt DRP needs 3,
+                                        // the 5-pt band stencils at the last row need 4)
+constexpr int MAX_PROBES = 1024;
+
+// tile flags
+constexpr uint32_t TILE_BAND = 1u;      // output region meets the 3 outer layers
+constexpr uint32_t TILE_MIXED = 2u;     // has non-fluid or out-of-grid outputs
+
+// Combined FP64 weight row entry of one cloud node: p_BP = sum l0 p,
+// Neumann row wp, Dirichlet row wd, free-extrapolation row wf.
+struct alignas(32) GW { double l0, wp, wd, wf; };
+
+// Per-instance descriptor read by every kernel (device copy in the arena).
+struct InstDesc {
+    void *q[3];                 // buffers Q^n, Q^a, Q^b; each holds planes p,u,v
+    long long plane;            // elements per plane = ny * pitch
+    const uint8_t *mask;        // node kind, ny x pitch (0 solid, 1 fluid, 2 ghost)
+    const uint32_t *tile_flags; // tiles_x * tiles_y
+    int nx, ny, pitch, tiles_x, tiles_y, ntiles;
+    int per_x, per_y;
+    double h, inv_h, dt;
+    double cx, cy;              // domain centre in index units ((n-1)/2)
+    // ghosts (Sec. 3.1-3.2)
+    int ng;
+    const int *g_target;        // ng
+    const int *g_start;         // ng + 1, entry ranges
+    const double2 *g_n;         // ng, wall normal (wall -> fluid)
+    const double2 *g_kappa;     // ng, (kappa_p, kappa_u)
+    const int *e_idx;           // entries: node index (j * pitch + i)
+    const GW *e_w;              // entries: (L0, w_p, w_d, w_f)
+    double *Xn;                 // ng x 2 ADE state at t_n
+    double *Xs;                 // ng x 2 ADE state of the current stage
+    double A[4], b[2], c[2];    // X' = A X + b p_BP, u_n = c . X
+    // monopole source (Sec. 4.3): s = amp * sigma_k * gx[i] * gy[j]
+    double s_amp, s_omega;
+    double G_re[4], G_im[4];    // stage k: sigma = sin(w t_n) G_re + cos(w t_n) G_im
+    const void *gx, *gy;        // source profiles in the bulk precision
+    // probes
+    int np, pcap;
+    const int *p_idx;           // np x 16 node indices (j * pitch + i)
+    const double *p_w;          // np x 16 weights
+    double *p_hist;             // pcap x np
+    long long *clock;           // [0] step in progress, [1] probe records, [2] status
+    double *scratch;            // reductions
+    double *staging;            // nx * ny doubles for host transfers
+    int precision;
+};
+
+// Host-side plan of one instance.
+struct Plan {
+    int nx = 0, ny = 0, pitch = 0;
+    int tiles_x = 0, tiles_y = 0;
+    std::vector<uint8_t> kind;          // ny * nx (host order, no pitch)
+    std::vector<uint32_t> tile_flags;
+    // ghosts
+    std::vector<int> g_target;          // j * nx + i (host order)
+    std::vector<int> g_start;
+    std::vector<double> g_meta;         // ng x 5: bpx, bpy, nx, ny, r
+    std::vector<int> g_m;
+    std::vector<double> g_kappa;        // ng x 2
+    std::vector<int> e_idx;             // host order j * nx + i
+    std::vector<double> e_w;            // 4 per entry
+    int n_reduced = 0;
+    int n_fluid = 0;
+    // ADE
+    int regime = 0;
+    double A[4] = {0, 0, 0, 0}, b[2] = {0, 0}, c[2] = {0, 0};
+    double ade_amp = 0;
+    // probes
+    std::vector<int> p_idx;             // np x 16 host order
+    std::vector<double> p_w;
+};
+
+struct Geometry {
+    int kind = 0;               // 0 none, 1 line, 2 cylinder
+    double a = 0, b = 0, c = 0; // line: point (a, b), angle c; cylinder: centre (a, b), radius c
+};
+
+struct Impedance {
+    bool rigid = true;
+    double R = 0, M = 0, K = 0;
+};
+
+// host set-up (lee_setup.cpp); returns LEE_* status, message in err
+int build_plan(int nx, int ny, double h, double x0, double y0, int per_x, int per_y, double dt,
+               const Geometry &geo, const Impedance &imp, const std::vector<double> &probe_xy,
+               Plan &plan, std::string &err);
+void stage_forcing_factors(double omega, double dt, double G_re[4], double G_im[4]);
+
+// kernel launchers (lee_kernels.cu); all return cudaError_t of the launch
+struct BatchView {
+    const InstDesc *inst;       // device array of instance descriptors
+    int ninst;
+    const int *tile_prefix;     // ninst + 1 (device)
+    const int *ghost_prefix;    // ninst + 1 (device)
+    const int *probe_inst;      // instances with probes (device), nprobe_inst entries
+    int nprobe_inst;
+    int total_tiles;
+    int total_ghosts;
+    int precision;
+};
+cudaError_t prepare_kernels(int precision);   // one-time function attributes (outside capture)
+cudaError_t launch_ghost(const BatchView &bv, int stage, cudaStream_t s);
+cudaError_t launch_stencil(const BatchView &bv, int stage, int persistent_ctas, cudaStream_t s);
+cudaError_t launch_probes(const BatchView &bv, cudaStream_t s);
+cudaError_t launch_init(const InstDesc *dinst, const InstDesc &h, int kind, const double *prm, cudaStream_t s);
+cudaError_t launch_to_staging(const InstDesc *dinst, const InstDesc &h, int which, int buf, cudaStream_t s);
+cudaError_t launch_from_staging(const InstDesc *dinst, const InstDesc &h, int which, cudaStream_t s);
+cudaError_t launch_energy(const InstDesc *dinst, const InstDesc &h, cudaStream_t s);
+long long launch_count();
+void count_launch(int n = 1);
+
+}  // namespace lee

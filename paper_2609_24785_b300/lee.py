@@ -1,0 +1,339 @@
+"""Thin ctypes binding of liblee (include/lee.h): same names as the C ABI,
+argument marshalling only.  Every step of the path runs in the library's CUDA
+kernels; there is no CPU fallback: importing this module without a built
+``liblee.so`` raises.
+
+``Solver`` bundles the calls of one solve: it allocates the device arena that
+``lee_plan`` asks for with PyTorch and binds it with a dedicated CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblee.so")
+
+LEE_OK, LEE_ERR_ARG, LEE_ERR_GEOMETRY, LEE_ERR_RANK, LEE_ERR_ADE_UNSTABLE, LEE_ERR_BUDGET, LEE_ERR_CUDA, \
+    LEE_ERR_DIVERGED, LEE_ERR_TIMEOUT = range(9)
+LEE_FP64, LEE_FP32 = 0, 1
+LEE_BC_RADIATION, LEE_BC_PERIODIC = 0, 1
+LEE_P, LEE_U, LEE_V = 0, 1, 2
+_STATUS = {1: "ARG", 2: "GEOMETRY", 3: "RANK", 4: "ADE_UNSTABLE", 5: "BUDGET", 6: "CUDA", 7: "DIVERGED", 8: "TIMEOUT"}
+
+
+class LeeError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"LEE_ERR_{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class lee_grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("h", C.c_double), ("cfl", C.c_double),
+                ("x0", C.c_double), ("y0", C.c_double), ("precision", C.c_int),
+                ("bc_x", C.c_int), ("bc_y", C.c_int)]
+
+
+class lee_sizes(C.Structure):
+    _fields_ = [("device_bytes", C.c_longlong), ("n_ghost", C.c_int), ("n_fluid", C.c_int),
+                ("n_entries", C.c_longlong), ("n_reduced", C.c_int), ("regime", C.c_int),
+                ("dt", C.c_double), ("ade_amplification", C.c_double), ("n_tiles", C.c_int)]
+
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+_llp = C.POINTER(C.c_longlong)
+_vp = C.c_void_p
+
+# name: (restype, argtypes) -- mirrors include/lee.h
+SIGNATURES = {
+    "lee_create": (C.c_int, [C.POINTER(_vp), C.POINTER(lee_grid)]),
+    "lee_destroy": (C.c_int, [_vp]),
+    "lee_last_error": (C.c_char_p, [_vp]),
+    "lee_set_wall_none": (C.c_int, [_vp]),
+    "lee_set_wall_line": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double]),
+    "lee_set_wall_cylinder": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double]),
+    "lee_set_impedance": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double]),
+    "lee_set_rigid": (C.c_int, [_vp]),
+    "lee_plan": (C.c_int, [_vp, C.POINTER(lee_sizes)]),
+    "lee_bind": (C.c_int, [_vp, _vp, C.c_longlong, _vp]),
+    "lee_init_pulse": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double, C.c_double]),
+    "lee_init_packet": (C.c_int, [_vp] + [C.c_double] * 6),
+    "lee_set_monopole": (C.c_int, [_vp] + [C.c_double] * 5),
+    "lee_write_field": (C.c_int, [_vp, C.c_int, _dp]),
+    "lee_set_probes": (C.c_int, [_vp, C.c_int, _dp, C.c_int]),
+    "lee_read_probes": (C.c_int, [_vp, _dp, _llp]),
+    "lee_step": (C.c_int, [_vp, C.c_longlong]),
+    "lee_sync": (C.c_int, [_vp]),
+    "lee_read_field": (C.c_int, [_vp, C.c_int, _dp]),
+    "lee_read_mask": (C.c_int, [_vp, C.POINTER(C.c_ubyte)]),
+    "lee_read_ade": (C.c_int, [_vp, _dp]),
+    "lee_get_step": (C.c_int, [_vp, _llp]),
+    "lee_energy": (C.c_int, [_vp, _dp]),
+    "lee_state_bytes": (C.c_int, [_vp, _llp]),
+    "lee_read_state": (C.c_int, [_vp, _vp]),
+    "lee_write_state": (C.c_int, [_vp, _vp]),
+    "lee_upload_state_async": (C.c_int, [_vp, _vp]),
+    "lee_download_probes_async": (C.c_int, [_vp, _dp, C.c_longlong, C.c_longlong]),
+    "lee_ghost_info": (C.c_int, [_vp, C.c_int, _ip, _dp, _ip, _ip]),
+    "lee_ghost_weights": (C.c_int, [_vp, C.c_int, _ip, _dp, _dp]),
+    "lee_batch_create": (C.c_int, [C.POINTER(_vp), C.c_int]),
+    "lee_batch_destroy": (C.c_int, [_vp]),
+    "lee_batch_add": (C.c_int, [_vp, _vp]),
+    "lee_batch_remove": (C.c_int, [_vp, _vp]),
+    "lee_batch_plan": (C.c_int, [_vp, _llp]),
+    "lee_batch_bind": (C.c_int, [_vp, _vp, C.c_longlong, _vp]),
+    "lee_batch_step": (C.c_int, [_vp, C.c_longlong]),
+    "lee_batch_last_error": (C.c_char_p, [_vp]),
+    "lee_batch_launch": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "lee_launch_count": (C.c_longlong, []),
+    "lee_version": (C.c_char_p, []),
+}
+
+_lib = None
+
+
+def load():
+    """Load liblee.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build() (no CPU fallback exists)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc, ctx=None, batch=None):
+    if rc != LEE_OK:
+        L = load()
+        if batch is not None:
+            msg = L.lee_batch_last_error(batch)
+        else:
+            msg = L.lee_last_error(ctx)
+        raise LeeError(rc, (msg or b"").decode())
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp)
+
+
+class Solver:
+    """One solve behind the C ABI: create -> wall/impedance/probes -> plan ->
+    bind (device arena from PyTorch, dedicated stream) -> init -> step -> read."""
+
+    def __init__(self, nx, ny, h, cfl=0.5, x0=0.0, y0=0.0, precision="fp64",
+                 periodic_x=False, periodic_y=False, device=None):
+        self.L = load()
+        self.nx, self.ny, self.h = nx, ny, h
+        self.precision = LEE_FP32 if precision in ("fp32", LEE_FP32) else LEE_FP64
+        g = lee_grid(nx, ny, h, cfl, x0, y0, self.precision,
+                     LEE_BC_PERIODIC if periodic_x else LEE_BC_RADIATION,
+                     LEE_BC_PERIODIC if periodic_y else LEE_BC_RADIATION)
+        self.ctx = _vp()
+        _check(self.L.lee_create(C.byref(self.ctx), C.byref(g)), None)
+        self.sizes = None
+        self.arena = None
+        self.stream = None
+        self.device = device
+        self._nprobe = 0
+
+    def __del__(self):
+        ctx = getattr(self, "ctx", None)
+        if ctx:
+            try:
+                if self.stream is not None:
+                    self.L.lee_sync(ctx)
+            finally:
+                self.L.lee_destroy(ctx)
+            self.ctx = None
+
+    def _c(self, rc):
+        _check(rc, self.ctx)
+
+    # ---- set-up
+    def set_wall_none(self):
+        self._c(self.L.lee_set_wall_none(self.ctx)); return self
+
+    def set_wall_line(self, xw, yw, angle):
+        self._c(self.L.lee_set_wall_line(self.ctx, xw, yw, angle)); return self
+
+    def set_wall_cylinder(self, xc, yc, r):
+        self._c(self.L.lee_set_wall_cylinder(self.ctx, xc, yc, r)); return self
+
+    def set_impedance(self, R, M, K):
+        self._c(self.L.lee_set_impedance(self.ctx, R, M, K)); return self
+
+    def set_rigid(self):
+        self._c(self.L.lee_set_rigid(self.ctx)); return self
+
+    def set_probes(self, xy, capacity):
+        xy = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1)
+        self._nprobe = len(xy) // 2
+        self._c(self.L.lee_set_probes(self.ctx, self._nprobe, _d(xy), int(capacity)))
+        return self
+
+    def plan(self):
+        s = lee_sizes()
+        self._c(self.L.lee_plan(self.ctx, C.byref(s)))
+        self.sizes = s
+        return s
+
+    def bind(self, arena=None, stream=None):
+        import torch
+        if self.sizes is None:
+            self.plan()
+        dev = self.device or torch.device("cuda", torch.cuda.current_device())
+        if arena is None:
+            arena = torch.empty(int(self.sizes.device_bytes), dtype=torch.uint8, device=dev)
+        self.arena = arena
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=dev)
+        self._c(self.L.lee_bind(self.ctx, arena.data_ptr(), arena.numel(), C.c_void_p(self.stream.cuda_stream)))
+        return self
+
+    # ---- state
+    def init_pulse(self, xs, ys, amp, halfwidth):
+        self._c(self.L.lee_init_pulse(self.ctx, xs, ys, amp, halfwidth)); return self
+
+    def init_packet(self, xs, ys, angle, amp, k, alpha):
+        self._c(self.L.lee_init_packet(self.ctx, xs, ys, angle, amp, k, alpha)); return self
+
+    def set_monopole(self, xs, ys, amp, halfwidth, omega):
+        self._c(self.L.lee_set_monopole(self.ctx, xs, ys, amp, halfwidth, omega)); return self
+
+    def write_field(self, which, arr):
+        a = np.ascontiguousarray(arr, dtype=np.float64).reshape(-1)
+        assert a.size == self.nx * self.ny
+        self._c(self.L.lee_write_field(self.ctx, which, _d(a)))
+
+    def step(self, n):
+        self._c(self.L.lee_step(self.ctx, int(n))); return self
+
+    def sync(self):
+        self._c(self.L.lee_sync(self.ctx))
+
+    # ---- read back
+    def field(self, which):
+        out = np.empty(self.nx * self.ny)
+        self._c(self.L.lee_read_field(self.ctx, which, _d(out)))
+        return out.reshape(self.ny, self.nx)
+
+    def mask(self):
+        out = np.empty(self.nx * self.ny, dtype=np.uint8)
+        self._c(self.L.lee_read_mask(self.ctx, out.ctypes.data_as(C.POINTER(C.c_ubyte))))
+        return out.reshape(self.ny, self.nx)
+
+    def ade(self):
+        ng = self.sizes.n_ghost
+        out = np.zeros(2 * max(ng, 1))
+        self._c(self.L.lee_read_ade(self.ctx, _d(out)))
+        return out[:2 * ng].reshape(-1, 2)
+
+    def steps_done(self):
+        v = C.c_longlong()
+        self._c(self.L.lee_get_step(self.ctx, C.byref(v)))
+        return v.value
+
+    def probes(self):
+        n = C.c_longlong()
+        self._c(self.L.lee_read_probes(self.ctx, None, C.byref(n)))
+        out = np.empty(max(n.value * self._nprobe, 1))
+        self._c(self.L.lee_read_probes(self.ctx, _d(out), C.byref(n)))
+        return out[:n.value * self._nprobe].reshape(n.value, self._nprobe)
+
+    def energy(self):
+        e = C.c_double()
+        self._c(self.L.lee_energy(self.ctx, C.byref(e)))
+        return e.value
+
+    def read_state(self):
+        nb = C.c_longlong()
+        self._c(self.L.lee_state_bytes(self.ctx, C.byref(nb)))
+        blob = np.empty(nb.value, dtype=np.uint8)
+        self._c(self.L.lee_read_state(self.ctx, blob.ctypes.data_as(_vp)))
+        return blob
+
+    def write_state(self, blob):
+        blob = np.ascontiguousarray(blob, dtype=np.uint8)
+        self._c(self.L.lee_write_state(self.ctx, blob.ctypes.data_as(_vp)))
+
+    # ---- plan export (host; no device needed)
+    def ghost(self, g):
+        t = C.c_int(); m = C.c_int(); n = C.c_int()
+        meta = np.empty(5)
+        self._c(self.L.lee_ghost_info(self.ctx, g, C.byref(t), _d(meta), C.byref(m), C.byref(n)))
+        idx = np.empty(n.value, dtype=np.int32)
+        w = np.empty(4 * n.value)
+        kap = np.empty(2)
+        self._c(self.L.lee_ghost_weights(self.ctx, g, idx.ctypes.data_as(_ip), _d(w), _d(kap)))
+        return dict(target=t.value, bp=meta[:2].copy(), n=meta[2:4].copy(), r=meta[4], m=m.value,
+                    cloud=idx, w=w.reshape(-1, 4), kappa=kap)
+
+
+class Batch:
+    """Several bound Solvers advanced by one ghost and one stencil launch per stage."""
+
+    def __init__(self, precision="fp32", stream=None):
+        import torch
+        self.L = load()
+        self.b = _vp()
+        self.precision = LEE_FP32 if precision in ("fp32", LEE_FP32) else LEE_FP64
+        _check(self.L.lee_batch_create(C.byref(self.b), self.precision))
+        self.members = []
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.arena = None
+
+    def __del__(self):
+        b = getattr(self, "b", None)
+        if b:
+            self.L.lee_batch_destroy(b)
+            self.b = None
+
+    def _c(self, rc):
+        _check(rc, batch=self.b)
+
+    def add(self, solver):
+        self._c(self.L.lee_batch_add(self.b, solver.ctx))
+        self.members.append(solver)
+        self._rebind()
+
+    def remove(self, solver):
+        self._c(self.L.lee_batch_remove(self.b, solver.ctx))
+        self.members.remove(solver)
+        self._rebind()
+
+    def _rebind(self):
+        import torch
+        nb = C.c_longlong()
+        self._c(self.L.lee_batch_plan(self.b, C.byref(nb)))
+        if self.arena is None or self.arena.numel() < nb.value:
+            self.arena = torch.empty(max(int(nb.value) * 2, 1 << 16), dtype=torch.uint8, device="cuda")
+            self._c(self.L.lee_batch_bind(self.b, self.arena.data_ptr(), self.arena.numel(),
+                                          C.c_void_p(self.stream.cuda_stream)))
+
+    def step(self, n):
+        # members' own streams must be idle before the batch stream uses their buffers
+        for s in self.members:
+            s.stream.synchronize()
+        self._c(self.L.lee_batch_step(self.b, int(n)))
+
+    def sync(self):
+        self.stream.synchronize()
+
+    def launch(self, stage, what):
+        """Measurement hook: one ghost (what=0) or stencil (what=1) launch of a stage."""
+        self._c(self.L.lee_batch_launch(self.b, int(stage), int(what)))
+
+
+def launch_count():
+    return load().lee_launch_count()
+
+
+def version():
+    return load().lee_version().decode()

@@ -1,0 +1,191 @@
+"""Seeded synthetic workloads (input recipes only, none of the method's
+arithmetic).  Shared by the tests, the benchmark and the oracle side.
+
+Units: grid spacing h = 0.01 in the impedance's length unit (one unit = 100
+cells), c0 = rho0 = 1, dt = cfl h.  Positions and widths given in cells are
+multiplied by h.  A ``Case`` describes one solve; ``apply_to(case, target)``
+calls the generic setter names that both the product binding (``lee.Solver``)
+and the oracle wrapper expose.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Callable, List, Optional, Tuple
+
+import numpy as np
+
+H = 0.01
+CFL = 0.5
+
+
+@dataclass
+class Case:
+    name: str
+    nx: int
+    ny: int
+    h: float = H
+    cfl: float = CFL
+    wall: Tuple = ("none",)            # ("line", xw, yw, angle) | ("cyl", xc, yc, r) | ("none",)
+    imp: Tuple = ("rigid",)            # ("rigid",) | ("msd", R, M, K)
+    init: Tuple = ("zero",)            # ("pulse", xs, ys, amp, w) | ("packet", xs, ys, ang, amp, k, alpha)
+    source: Optional[Tuple] = None     # ("monopole", xs, ys, amp, w, omega)
+    probes: np.ndarray = field(default_factory=lambda: np.zeros((0, 2)))
+    steps: int = 100
+    periodic: Tuple[bool, bool] = (False, False)
+
+    @property
+    def centre(self):
+        return ((self.nx - 1) / 2 * self.h, (self.ny - 1) / 2 * self.h)
+
+    @property
+    def points(self):
+        return self.nx * self.ny
+
+
+def flat_wall(n=128, angle_deg=30.0, steps=400, R=1.0, M=0.05, K=5.0, rigid=False) -> Case:
+    """Inclined impedance wall through the centre, Gaussian pulse 20 cells off
+    the wall on the fluid side (half-width 3 cells, amplitude 1e-3); probes on
+    the normal through the pulse centre, 2..16 cells from the wall."""
+    c = ((n - 1) / 2 * H, (n - 1) / 2 * H)
+    th = math.radians(angle_deg)
+    nrm = np.array([-math.sin(th), math.cos(th)])
+    src = np.array(c) + 20 * H * nrm
+    probes = np.array([np.array(c) + d * H * nrm for d in (2, 4, 6, 8, 10, 12, 14, 16)])
+    return Case("flat_wall_%d" % n, n, n, wall=("line", c[0], c[1], th),
+                imp=("rigid",) if rigid else ("msd", R, M, K),
+                init=("pulse", src[0], src[1], 1e-3, 3 * H), probes=probes, steps=steps)
+
+
+def cylinder_pulse(n=1024, steps=3000, R=2.0, M=0.02, K=1.0, rigid=False, nx=None, ny=None) -> Case:
+    """Cylinder of radius n/20.48 cells (50 at n = 1024) at the centre, Gaussian
+    pulse of half-width 4n/1024 cells and amplitude 1 at n/10.24 cells on +x;
+    8 probes on a ring of 1.5 radii.  The physical problem is the same for every
+    n when h = 0.01 * 1024 / n (refinement sweeps pass h explicitly)."""
+    nx = nx or n
+    ny = ny or n
+    c = ((nx - 1) / 2 * H, (ny - 1) / 2 * H)
+    r = n / 20.48 * H
+    w = 4.0 * n / 1024 * H
+    xs = c[0] + n / 10.24 * H
+    ang = np.arange(8) * math.pi / 4
+    probes = np.stack([c[0] + 1.5 * r * np.cos(ang), c[1] + 1.5 * r * np.sin(ang)], 1)
+    return Case("cylinder_pulse_%dx%d" % (nx, ny), nx, ny, wall=("cyl", c[0], c[1], r),
+                imp=("rigid",) if rigid else ("msd", R, M, K),
+                init=("pulse", xs, c[1], 1.0, w), probes=probes, steps=steps)
+
+
+def monopole(n=2048, steps=20000, R=1.0, M=0.1, K=10.0, radius_cells=None, src_cells=None,
+             nring=256) -> Case:
+    """Cylinder of radius n/20.48 cells scattering a harmonic monopole at
+    3 radii on +x (half-width 3 cells, amplitude 1, 20 points per wavelength);
+    probe ring of nring points at 1.1 radii."""
+    c = ((n - 1) / 2 * H, (n - 1) / 2 * H)
+    rc = (radius_cells if radius_cells is not None else n / 20.48) * H
+    xs = c[0] + (src_cells if src_cells is not None else 3 * n / 20.48) * H
+    omega = 2 * math.pi / (20 * H)
+    ang = np.arange(nring) * 2 * math.pi / nring
+    probes = np.stack([c[0] + 1.1 * rc * np.cos(ang), c[1] + 1.1 * rc * np.sin(ang)], 1)
+    return Case("monopole_%d" % n, n, n, wall=("cyl", c[0], c[1], rc), imp=("msd", R, M, K),
+                source=("monopole", xs, c[1], 1.0, 3 * H, omega), probes=probes, steps=steps)
+
+
+SWEEP_SIZES = (256, 384, 512, 768, 1024)
+
+
+def sweep(count=512, seed=24785, steps=2000, accept: Optional[Callable[[Case], bool]] = None,
+          sizes=SWEEP_SIZES) -> Tuple[List[Case], int]:
+    """Batched parametric sweep: grid n uniform in `sizes`, cylinder radius 0.1 n
+    cells at the centre, pulse (half-width 4 cells) at 0.25 n cells on +x, R, M,
+    K log-uniform in [0.2, 5], [0.005, 0.2], [0.5, 20].  Draws rejected by
+    `accept` (e.g. an unstable wall ODE) are redrawn from the same stream;
+    returns (cases, rejected)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out, rejected = [], 0
+    while len(out) < count:
+        n = int(rng.choice(sizes))
+        R = float(np.exp(rng.uniform(np.log(0.2), np.log(5.0))))
+        M = float(np.exp(rng.uniform(np.log(0.005), np.log(0.2))))
+        K = float(np.exp(rng.uniform(np.log(0.5), np.log(20.0))))
+        c = ((n - 1) / 2 * H, (n - 1) / 2 * H)
+        case = Case("sweep_%d_n%d" % (len(out), n), n, n, wall=("cyl", c[0], c[1], 0.1 * n * H),
+                    imp=("msd", R, M, K), init=("pulse", c[0] + 0.25 * n * H, c[1], 1.0, 4 * H),
+                    probes=np.array([[c[0] + 0.15 * n * H, c[1]]]), steps=steps)
+        if accept is None or accept(case):
+            out.append(case)
+        else:
+            rejected += 1
+    return out, rejected
+
+
+SERVE_SIZES = (256, 384, 512, 768, 1024, 1536, 2048)
+
+
+def serving_trace(rate=200.0, duration=1.0, seed=24786, accept=None, sizes=SERVE_SIZES,
+                  steps_range=(1000, 10000)) -> List[Tuple[float, Case]]:
+    """Poisson arrivals (mean `rate` per second over `duration` seconds) of mixed
+    solves: half flat walls through the centre at an angle U[0, 60] deg, half
+    cylinders of radius U[0.05, 0.15] n; pulse of half-width 4 cells at a
+    uniform position at least 20 cells from the wall and the edges; R, M, K as
+    in the sweep; steps uniform in steps_range."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t, out = 0.0, []
+    while True:
+        t += float(rng.exponential(1.0 / rate))
+        if t > duration:
+            break
+        while True:
+            n = int(rng.choice(sizes))
+            c = ((n - 1) / 2 * H, (n - 1) / 2 * H)
+            R = float(np.exp(rng.uniform(np.log(0.2), np.log(5.0))))
+            M = float(np.exp(rng.uniform(np.log(0.005), np.log(0.2))))
+            K = float(np.exp(rng.uniform(np.log(0.5), np.log(20.0))))
+            steps = int(rng.integers(steps_range[0], steps_range[1] + 1))
+            if rng.uniform() < 0.5:
+                th = math.radians(float(rng.uniform(0, 60)))
+                wall = ("line", c[0] + 0.37 * H, c[1], th)
+                nrm = np.array([-math.sin(th), math.cos(th)])
+                # fluid side, 20..(n/2 - 20) cells from the wall along the normal
+                d = float(rng.uniform(20, max(21, n / 2 - 24)))
+                pos = np.array(c) + d * H * nrm
+            else:
+                rr = float(rng.uniform(0.05, 0.15)) * n
+                wall = ("cyl", c[0], c[1], rr * H)
+                ang = float(rng.uniform(0, 2 * math.pi))
+                d = float(rng.uniform(rr + 20, max(rr + 21, n / 2 - 24)))
+                pos = np.array(c) + d * H * np.array([math.cos(ang), math.sin(ang)])
+            case = Case("serve_%d_n%d" % (len(out), n), n, n, wall=wall, imp=("msd", R, M, K),
+                        init=("pulse", pos[0], pos[1], 1.0, 4 * H),
+                        probes=np.array([[pos[0], pos[1]]]), steps=steps)
+            if accept is None or accept(case):
+                break
+        out.append((t, case))
+    return out
+
+
+def apply_to(case: Case, target):
+    """Set geometry, impedance and probes on a product Solver or an oracle via
+    their common setter names (the caller then plans / sets up)."""
+    w = case.wall
+    if w[0] == "line":
+        (target.set_wall_line if hasattr(target, "set_wall_line") else target.set_line)(*w[1:])
+    elif w[0] == "cyl":
+        (target.set_wall_cylinder if hasattr(target, "set_wall_cylinder") else target.set_cylinder)(*w[1:])
+    else:
+        (target.set_wall_none if hasattr(target, "set_wall_none") else target.set_none)()
+    if case.imp[0] == "msd":
+        target.set_impedance(*case.imp[1:])
+    else:
+        target.set_rigid()
+    return target
+
+
+def apply_state(case: Case, target):
+    """Initial field and source (after plan/bind or set-up)."""
+    if case.source is not None:
+        target.set_monopole(*case.source[1:])
+    if case.init[0] == "pulse":
+        target.init_pulse(*case.init[1:])
+    elif case.init[0] == "packet":
+        target.init_packet(*case.init[1:])
+    return target

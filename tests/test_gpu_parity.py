@@ -1,0 +1,154 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.  Bars: relative L2 over the fluid nodes of (p, u, v)
+<= 1e-12 with FP64 bulk and <= 1e-5 with FP32 bulk (FP64 ghost weights and
+ADE), after the stated step counts; ADE states and probe histories to the
+same bars."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2609_24785_b300 import lee, workloads
+from _helpers import make_oracle, make_solver, field_error, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+def _check(case, precision, steps=None, ade=True, probes=True):
+    steps = case.steps if steps is None else steps
+    s = make_solver(case, precision)
+    o = make_oracle(case)
+    s.step(steps)
+    s.sync()
+    o.run(steps)
+    assert s.steps_done() == steps == o.step
+    err = field_error(s, o)
+    assert err <= TOL[precision], (case.name, precision, err)
+    if ade and o.n_ghost and case.imp[0] == "msd":
+        ea = rel_l2(s.ade(), o.ade())
+        assert ea <= TOL[precision], ("ade", ea)
+    if probes and len(case.probes):
+        ep = rel_l2(s.probes(), o.probes())
+        assert ep <= TOL[precision], ("probes", ep)
+    return s, o, err
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_flat_wall_128_critical_ade(precision, cuda_device):
+    """Inclined impedance wall, 128^2, R = 2 sqrt(KM) (double pole), 400 steps."""
+    _check(workloads.flat_wall(128), precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_cylinder_ragged_real_poles(precision, cuda_device):
+    """Cylinder pulse on a ragged 200 x 136 grid (partial tiles in x and y),
+    two real poles (one stiff), 300 steps."""
+    case = workloads.cylinder_pulse(256, nx=200, ny=136)
+    _check(case, precision, steps=300)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_monopole_complex_pair(precision, cuda_device):
+    """Harmonic monopole (20 points per wavelength) on a cylinder, complex pole
+    pair, 400 steps: exercises the stage forcing moments."""
+    case = workloads.monopole(160, radius_cells=14.3, src_cells=38, nring=16)
+    _check(case, precision, steps=400)
+
+
+def test_rigid_cylinder_packet(cuda_device):
+    case = workloads.cylinder_pulse(192)
+    case.imp = ("rigid",)
+    c = case.centre
+    case.init = ("packet", c[0] + 30 * case.h, c[1], math.pi, 1.0, 1.0 / (16 * case.h), 1.0 / (6 * case.h))
+    _check(case, "fp64", steps=200)
+
+
+def test_periodic_flat_wall(cuda_device):
+    """Quasi-1D wall normal to x with periodic y (the App. A set-up)."""
+    h = 0.01
+    case = workloads.Case("periodic", 330, 8, wall=("line", 300.5 * h, 0.0, math.pi / 2),
+                          imp=("msd", 0.2, 0.025, 40.0),
+                          init=("packet", 230.5 * h, 0.0, 0.0, 2.0, 0.0, 1.0 / (6 * h)),
+                          probes=np.array([[265.5 * h, 3 * h]]), steps=300, periodic=(False, True))
+    _check(case, "fp64")
+
+
+def test_no_wall_and_small_grid(cuda_device):
+    case = workloads.Case("free", 40, 24, init=("pulse", 0.2, 0.12, 1.0, 0.03), steps=50)
+    _check(case, "fp64")
+    case = workloads.Case("tiny", 8, 8, init=("pulse", 0.035, 0.035, 1.0, 0.02), steps=20)
+    _check(case, "fp64")
+
+
+def test_energy_matches_oracle(cuda_device):
+    case = workloads.cylinder_pulse(256)
+    s = make_solver(case, "fp64")
+    o = make_oracle(case)
+    s.step(100)
+    o.run(100)
+    assert abs(s.energy() - o.energy()) <= 1e-12 * o.energy()
+
+
+def test_checkpoint_resume_bitwise(cuda_device):
+    case = workloads.cylinder_pulse(256)
+    s = make_solver(case, "fp32")
+    s.step(40)
+    blob = s.read_state()
+    s.step(40)
+    ref = [s.field(f) for f in range(3)]
+    ade = s.ade()
+    s.write_state(blob)
+    s.step(40)
+    for f in range(3):
+        assert np.array_equal(s.field(f), ref[f])
+    assert np.array_equal(s.ade(), ade)
+    assert s.steps_done() == 80
+
+
+def test_graph_and_eager_paths_agree(cuda_device, monkeypatch):
+    """Stepping 1 + 8 + 3 steps (graphs of 1 and 8 steps) equals 12 steps in one call."""
+    case = workloads.cylinder_pulse(256)
+    a = make_solver(case, "fp32")
+    b = make_solver(case, "fp32")
+    a.step(12)
+    for n in (1, 8, 3):
+        b.step(n)
+    for f in range(3):
+        assert np.array_equal(a.field(f), b.field(f))
+
+
+def test_batch_equals_solo_and_oracle(cuda_device):
+    """Three uneven instances advanced in one batch (one ghost and one stencil
+    launch per stage) give bitwise the solo results, and match the oracle."""
+    cases = [workloads.cylinder_pulse(256), workloads.cylinder_pulse(256, nx=192, ny=160, R=0.5, M=0.01, K=3.0),
+             workloads.flat_wall(128)]
+    steps = 60
+    solo = []
+    for c in cases:
+        s = make_solver(c, "fp64")
+        s.step(steps)
+        solo.append([s.field(f) for f in range(3)] + [s.ade()])
+    batch = lee.Batch("fp64")
+    members = [make_solver(c, "fp64") for c in cases]
+    for m in members:
+        batch.add(m)
+    batch.step(steps)
+    batch.sync()
+    for c, m, ref in zip(cases, members, solo):
+        for f in range(3):
+            assert np.array_equal(m.field(f), ref[f]), c.name
+        assert np.array_equal(m.ade(), ref[3])
+        o = make_oracle(c)
+        o.run(steps)
+        assert field_error(m, o) <= TOL["fp64"]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_full_size_cylinder_1024(precision, cuda_device):
+    """The 1024^2 cylinder-pulse workload at full size (the timed launch
+    configuration), compared over every node after 100 steps."""
+    case = workloads.cylinder_pulse(1024)
+    _check(case, precision, steps=100, probes=False)
