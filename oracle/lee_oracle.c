@@ -262,19 +262,20 @@ double orc_stage_forcing(double omega, double tn, double dt, int k)
 { return stage_forcing(omega, tn, dt, k); }
 
 /* ------------------------------------------------------------ setup */
-/* Lagrange basis on nodes sg[0..m]: value and derivative of basis i at s. */
-static double lag_val(const double *sg, int m, int i, double s)
+/* Lagrange basis on nodes sg[0..m]: value and derivative of basis i at s
+ * (extended precision, rounded to FP64 by the caller). */
+static long double lag_val(const long double *sg, int m, int i, long double s)
 {
-    double v = 1.0;
+    long double v = 1.0L;
     for (int j = 0; j <= m; j++) if (j != i) v *= (s - sg[j]) / (sg[i] - sg[j]);
     return v;
 }
-static double lag_der(const double *sg, int m, int i, double s)
+static long double lag_der(const long double *sg, int m, int i, long double s)
 {
-    double d = 0.0;
+    long double d = 0.0L;
     for (int k = 0; k <= m; k++) {
         if (k == i) continue;
-        double t = 1.0 / (sg[i] - sg[k]);
+        long double t = 1.0L / (sg[i] - sg[k]);
         for (int j = 0; j <= m; j++) if (j != i && j != k) t *= (s - sg[j]) / (sg[i] - sg[j]);
         d += t;
     }
@@ -290,69 +291,73 @@ static int monomials(int k, int *al, int *be)
     return n;
 }
 
-static double ipow(double x, int e) { double r = 1.0; while (e-- > 0) r *= x; return r; }
 
 /*
  * Least-squares read-out rows (Eqs. ns-poly2d .. ns-readout).  The fit
  * a = (V^T V)^{-1} V^T f is evaluated through a thin QR of the column-scaled
  * Vandermonde matrix computed by modified Gram-Schmidt with one
- * re-orthogonalisation pass; L_i = v(P_i)^T a-map, i.e.
- * L_i = Q R^{-T} D v(P_i) with D the column scaling.
+ * re-orthogonalisation pass, in extended precision (long double) and rounded
+ * to FP64 at the end; L_i = v(P_i)^T a-map, i.e. L_i = Q R^{-T} D v(P_i)
+ * with D the column scaling.
  * Returns 0 on success, 1 if the cloud is rank deficient at this degree.
  */
+typedef long double xreal;
+
+static xreal xpow(xreal x, int e) { xreal r = 1.0L; while (e-- > 0) r *= x; return r; }
+
 static int lsq_rows(int N, const double *xp, const double *yp, int k, double *L)
 {
     int al[15], be[15];
     int nm = monomials(k, al, be);
     if (N < nm) return 1;
-    double *Q = (double *)malloc(sizeof(double) * N * nm);
-    double R[15][15];
-    double D[15];
+    xreal *Q = (xreal *)malloc(sizeof(xreal) * N * nm);
+    xreal R[15][15];
+    xreal D[15];
     memset(R, 0, sizeof(R));
     for (int j = 0; j < nm; j++) {
-        double s = 0.0;
+        xreal s = 0.0L;
         for (int e = 0; e < N; e++) {
-            double v = ipow(xp[e], al[j]) * ipow(yp[e], be[j]);
+            xreal v = xpow(xp[e], al[j]) * xpow(yp[e], be[j]);
             Q[e * nm + j] = v;
             s += v * v;
         }
-        D[j] = s > 0 ? 1.0 / sqrt(s) : 1.0;
+        D[j] = s > 0 ? 1.0L / sqrtl(s) : 1.0L;
         for (int e = 0; e < N; e++) Q[e * nm + j] *= D[j];
     }
     for (int j = 0; j < nm; j++) {
         for (int pass = 0; pass < 2; pass++) {
             for (int i = 0; i < j; i++) {
-                double dot = 0.0;
+                xreal dot = 0.0L;
                 for (int e = 0; e < N; e++) dot += Q[e * nm + i] * Q[e * nm + j];
                 R[i][j] += dot;
                 for (int e = 0; e < N; e++) Q[e * nm + j] -= dot * Q[e * nm + i];
             }
         }
-        double nrm = 0.0;
+        xreal nrm = 0.0L;
         for (int e = 0; e < N; e++) nrm += Q[e * nm + j] * Q[e * nm + j];
-        nrm = sqrt(nrm);
+        nrm = sqrtl(nrm);
         R[j][j] = nrm;
         if (nrm > 0) for (int e = 0; e < N; e++) Q[e * nm + j] /= nrm;
     }
-    double rmax = 0.0, rmin = 1e300;
+    xreal rmax = 0.0L, rmin = 1e300L;
     for (int j = 0; j < nm; j++) {
-        double a = fabs(R[j][j]);
+        xreal a = fabsl(R[j][j]);
         if (a > rmax) rmax = a;
         if (a < rmin) rmin = a;
     }
-    if (!(rmin > 1e-10 * rmax)) { free(Q); return 1; }
+    if (!(rmin > 1e-10L * rmax)) { free(Q); return 1; }
     for (int i = 0; i <= k; i++) {
         /* v(P_i): x' = i, y' = 0 */
-        double z[15];
+        xreal z[15];
         for (int j = 0; j < nm; j++) {
-            double v = (be[j] == 0 ? ipow((double)i, al[j]) : 0.0) * D[j];
+            xreal v = (be[j] == 0 ? xpow((xreal)i, al[j]) : 0.0L) * D[j];
             for (int l = 0; l < j; l++) v -= R[l][j] * z[l];
             z[j] = v / R[j][j];              /* R^T z = D v  (forward) */
         }
         for (int e = 0; e < N; e++) {
-            double s = 0.0;
+            xreal s = 0.0L;
             for (int j = 0; j < nm; j++) s += Q[e * nm + j] * z[j];
-            L[i * N + e] = s;
+            L[i * N + e] = (double)s;
         }
     }
     free(Q);
@@ -426,14 +431,14 @@ static int build_ghost(orc_t *o, orc_ghost *G, int gi, int gj)
     /* Step 2 of Sec. 3.1: Lagrange factors along the normal.
      * Dirichlet / Neumann: nodes {-r, 1..m}, evaluated (value / slope) at s = 0.
      * Free: nodes {0..m}, evaluated at s = -r. */
-    double sg[5], s0[5];
-    sg[0] = -G->r;
-    for (int i = 1; i <= k; i++) sg[i] = (double)i;
-    for (int i = 0; i <= k; i++) s0[i] = (double)i;
+    long double sg[5], s0[5];
+    sg[0] = -(long double)G->r;
+    for (int i = 1; i <= k; i++) sg[i] = i;
+    for (int i = 0; i <= k; i++) s0[i] = i;
     for (int i = 0; i <= k; i++) {
-        G->c[i] = lag_val(sg, k, i, 0.0);
-        G->ct[i] = lag_der(sg, k, i, 0.0);
-        G->ell[i] = lag_val(s0, k, i, -G->r);
+        G->c[i] = (double)lag_val(sg, k, i, 0.0L);
+        G->ct[i] = (double)lag_der(sg, k, i, 0.0L);
+        G->ell[i] = (double)lag_val(s0, k, i, -(long double)G->r);
     }
     return 0;
 }
@@ -569,11 +574,11 @@ int orc_set_probes(orc_t *o, int n, const double *xy, long cap)
                 if (o->kind[(j0 + b) * o->nx + i0 + a] != 1) ok = 0;
         if (ok) {
             /* 4 x 4 tensor Lagrange interpolation of degree 3 */
-            double sn[4] = {0, 1, 2, 3};
+            long double sn[4] = {0, 1, 2, 3};
             for (int b = 0; b < 4; b++)
                 for (int a = 0; a < 4; a++) {
                     o->pidx[16 * p + 4 * b + a] = (j0 + b) * o->nx + i0 + a;
-                    o->pw[16 * p + 4 * b + a] = lag_val(sn, 3, a, xi) * lag_val(sn, 3, b, eta);
+                    o->pw[16 * p + 4 * b + a] = (double)(lag_val(sn, 3, a, xi) * lag_val(sn, 3, b, eta));
                 }
         } else {
             int i = (int)floor(fx + 0.5), j = (int)floor(fy + 0.5);

@@ -57,70 +57,75 @@ inline void axis_footprint(int i, int n, int per, int &lo, int &hi) {
     else { lo = i - 3; hi = i + 3; }
 }
 
+// Extended precision for the least-squares and Lagrange factors; the weight
+// rows are rounded to FP64 once, after they are combined.
+using xr = long double;
+
 // Householder QR of the column-scaled N x nm Vandermonde matrix and the
 // read-out rows L_i = v(P_i)^T V^+ for P_i = (i, 0), i = 0..k.
 // Returns false when |R_jj| spans more than 1e10 (rank deficient).
-bool readout_rows(int N, const double *xp, const double *yp, int k, double *L /* (k+1) x N */) {
+bool readout_rows(int N, const double *xp, const double *yp, int k, xr *L /* (k+1) x N */) {
     int ea[15], eb[15], nm = 0;
     for (int d = 0; d <= k; ++d)
         for (int a = d; a >= 0; --a) { ea[nm] = a; eb[nm] = d - a; ++nm; }
     if (N < nm) return false;
-    std::vector<double> V((size_t)N * nm);           // column-major: V[j * N + e]
-    double scale[15];
+    auto pw = [](xr x, int e) { xr r = 1.0L; while (e-- > 0) r *= x; return r; };
+    std::vector<xr> V((size_t)N * nm);               // column-major: V[j * N + e]
+    xr scale[15];
     for (int j = 0; j < nm; ++j) {
-        double s2 = 0.0;
+        xr s2 = 0.0L;
         for (int e = 0; e < N; ++e) {
-            double v = std::pow(xp[e], ea[j]) * std::pow(yp[e], eb[j]);
+            xr v = pw(xp[e], ea[j]) * pw(yp[e], eb[j]);
             V[(size_t)j * N + e] = v;
             s2 += v * v;
         }
-        scale[j] = s2 > 0.0 ? 1.0 / std::sqrt(s2) : 1.0;
+        scale[j] = s2 > 0.0L ? 1.0L / std::sqrt(s2) : 1.0L;
         for (int e = 0; e < N; ++e) V[(size_t)j * N + e] *= scale[j];
     }
-    std::vector<double> hv((size_t)N * nm, 0.0);       // unit Householder vectors
-    double Rd[15];
-    std::vector<double> R((size_t)nm * nm, 0.0);
+    std::vector<xr> hv((size_t)N * nm, 0.0L);         // unit Householder vectors
+    xr Rd[15];
+    std::vector<xr> R((size_t)nm * nm, 0.0L);
     for (int j = 0; j < nm; ++j) {
-        double *col = &V[(size_t)j * N];
-        double nrm = 0.0;
+        xr *col = &V[(size_t)j * N];
+        xr nrm = 0.0L;
         for (int e = j; e < N; ++e) nrm += col[e] * col[e];
         nrm = std::sqrt(nrm);
-        double alpha = col[j] > 0 ? -nrm : nrm;
-        double *v = &hv[(size_t)j * N];
+        xr alpha = col[j] > 0 ? -nrm : nrm;
+        xr *v = &hv[(size_t)j * N];
         for (int e = j; e < N; ++e) v[e] = col[e];
         v[j] -= alpha;
-        double vn = 0.0;
+        xr vn = 0.0L;
         for (int e = j; e < N; ++e) vn += v[e] * v[e];
         vn = std::sqrt(vn);
-        if (vn > 0.0) for (int e = j; e < N; ++e) v[e] /= vn;
+        if (vn > 0.0L) for (int e = j; e < N; ++e) v[e] /= vn;
         // apply H_j = I - 2 v v^T to the remaining columns
         for (int jj = j; jj < nm; ++jj) {
-            double *cc = &V[(size_t)jj * N];
-            double dot = 0.0;
+            xr *cc = &V[(size_t)jj * N];
+            xr dot = 0.0L;
             for (int e = j; e < N; ++e) dot += v[e] * cc[e];
-            for (int e = j; e < N; ++e) cc[e] -= 2.0 * dot * v[e];
+            for (int e = j; e < N; ++e) cc[e] -= 2.0L * dot * v[e];
         }
         for (int i = 0; i <= j; ++i) R[(size_t)i * nm + j] = V[(size_t)j * N + i];
         Rd[j] = std::fabs(R[(size_t)j * nm + j]);
     }
-    double rmax = *std::max_element(Rd, Rd + nm), rmin = *std::min_element(Rd, Rd + nm);
-    if (!(rmin > 1e-10 * rmax)) return false;
-    std::vector<double> y(N);
+    xr rmax = *std::max_element(Rd, Rd + nm), rmin = *std::min_element(Rd, Rd + nm);
+    if (!(rmin > 1e-10L * rmax)) return false;
+    std::vector<xr> y(N);
     for (int i = 0; i <= k; ++i) {
-        double z[15];
+        xr z[15];
         // R^T z = D v(P_i), v(P_i) has x' = i, y' = 0
         for (int j = 0; j < nm; ++j) {
-            double rhs = (eb[j] == 0 ? std::pow((double)i, ea[j]) : 0.0) * scale[j];
+            xr rhs = (eb[j] == 0 ? pw((xr)i, ea[j]) : 0.0L) * scale[j];
             for (int l = 0; l < j; ++l) rhs -= R[(size_t)l * nm + j] * z[l];
             z[j] = rhs / R[(size_t)j * nm + j];
         }
-        std::fill(y.begin(), y.end(), 0.0);
+        std::fill(y.begin(), y.end(), 0.0L);
         for (int j = 0; j < nm; ++j) y[j] = z[j];
         for (int j = nm - 1; j >= 0; --j) {            // y = H_0 ... H_{nm-1} [z; 0]
-            const double *v = &hv[(size_t)j * N];
-            double dot = 0.0;
+            const xr *v = &hv[(size_t)j * N];
+            xr dot = 0.0L;
             for (int e = j; e < N; ++e) dot += v[e] * y[e];
-            for (int e = j; e < N; ++e) y[e] -= 2.0 * dot * v[e];
+            for (int e = j; e < N; ++e) y[e] -= 2.0L * dot * v[e];
         }
         for (int e = 0; e < N; ++e) L[(size_t)i * N + e] = y[e];
     }
@@ -128,18 +133,18 @@ bool readout_rows(int N, const double *xp, const double *yp, int k, double *L /*
 }
 
 // Lagrange basis on nodes {first..m} (integers), value at s.
-double lag(int first, int m, int i, double s) {
-    double v = 1.0;
-    for (int j = first; j <= m; ++j) if (j != i) v *= (s - j) / double(i - j);
+xr lag(int first, int m, int i, xr s) {
+    xr v = 1.0L;
+    for (int j = first; j <= m; ++j) if (j != i) v *= (s - j) / xr(i - j);
     return v;
 }
 // derivative at s of the same basis
-double lag_d(int first, int m, int i, double s) {
-    double d = 0.0;
+xr lag_d(int first, int m, int i, xr s) {
+    xr d = 0.0L;
     for (int k = first; k <= m; ++k) {
         if (k == i) continue;
-        double t = 1.0 / double(i - k);
-        for (int j = first; j <= m; ++j) if (j != i && j != k) t *= (s - j) / double(i - j);
+        xr t = 1.0L / xr(i - k);
+        for (int j = first; j <= m; ++j) if (j != i && j != k) t *= (s - j) / xr(i - j);
         d += t;
     }
     return d;
@@ -153,22 +158,22 @@ double lag_d(int first, int m, int i, double s) {
 // The Neumann polynomial is written Q = sum_i f_i lh_i + beta w with lh the
 // Lagrange basis on {1..m} and w(s) = prod_{i=1..m} (s - i), which vanishes
 // on the nodes; Q'(0) = h g_n fixes beta.
-void normal_factors(int m, double r, double *dir, double &kd, double *neu, double &kn) {
-    const double s = -r;
+void normal_factors(int m, double r, xr *dir, xr &kd, xr *neu, xr &kn) {
+    const xr s = -(xr)r;
     for (int i = 0; i <= m; ++i) dir[i] = lag(0, m, i, s);
     kd = dir[0];
-    double w_s = 1.0, w_d0 = 0.0;
+    xr w_s = 1.0L, w_d0 = 0.0L;
     for (int i = 1; i <= m; ++i) w_s *= (s - i);
     for (int k = 1; k <= m; ++k) {
-        double t = 1.0;
-        for (int j = 1; j <= m; ++j) if (j != k) t *= (0.0 - j);
+        xr t = 1.0L;
+        for (int j = 1; j <= m; ++j) if (j != k) t *= (0.0L - j);
         w_d0 += t;
     }
     kn = w_s / w_d0;
-    neu[0] = 0.0;
+    neu[0] = 0.0L;
     for (int i = 1; i <= m; ++i) {
-        double lh = (m == 1) ? 1.0 : lag(1, m, i, s);
-        double lhd = (m == 1) ? 0.0 : lag_d(1, m, i, 0.0);
+        xr lh = (m == 1) ? 1.0L : lag(1, m, i, s);
+        xr lhd = (m == 1) ? 0.0L : lag_d(1, m, i, 0.0L);
         neu[i] = lh - lhd * kn;
     }
 }
@@ -282,25 +287,26 @@ int build_plan(int nx, int ny, double h, double x0, double y0, int per_x, int pe
         }
         if (G.status) continue;
         (void)RN; (void)RT;
-        std::vector<double> L((size_t)(KMAX + 1) * (N > 0 ? N : 1));
+        std::vector<xr> L((size_t)(KMAX + 1) * (N > 0 ? N : 1));
         int m = KMAX;
         while (m >= 1 && !readout_rows(N, xp, yp, m, L.data())) --m;
         if (m < 1) { G.status = LEE_ERR_RANK; continue; }
         G.m = m;
-        double dir[KMAX + 1], neu[KMAX + 1], kd, kn;
+        xr dir[KMAX + 1], neu[KMAX + 1], kd, kn;
         normal_factors(m, r, dir, kd, neu, kn);
-        G.kp = kn * h;            // multiplies dp/dn at BP
-        G.ku = kd;                // multiplies w = u.n at BP
+        G.kp = (double)(kn * (xr)h);   // multiplies dp/dn at BP
+        G.ku = (double)kd;             // multiplies w = u.n at BP
         G.w.assign((size_t)4 * N, 0.0);
         for (int e = 0; e < N; ++e) {
-            double l0 = L[e], wp = 0.0, wd = 0.0, wf = dir[0] * L[e];
+            xr l0 = L[e], wp = 0.0L, wd = 0.0L, wf = dir[0] * L[e];
             for (int i = 1; i <= m; ++i) {
-                const double li = L[(size_t)i * N + e];
+                const xr li = L[(size_t)i * N + e];
                 wp += neu[i] * li;
                 wd += dir[i] * li;
                 wf += dir[i] * li;
             }
-            G.w[4 * e + 0] = l0; G.w[4 * e + 1] = wp; G.w[4 * e + 2] = wd; G.w[4 * e + 3] = wf;
+            G.w[4 * e + 0] = (double)l0; G.w[4 * e + 1] = (double)wp;
+            G.w[4 * e + 2] = (double)wd; G.w[4 * e + 3] = (double)wf;
         }
     }
     P.g_start.assign(ng + 1, 0);
@@ -386,7 +392,7 @@ int build_plan(int nx, int ny, double h, double x0, double y0, int per_x, int pe
             for (int b = 0; b < 4; ++b)
                 for (int a = 0; a < 4; ++a) {
                     P.p_idx[16 * p + 4 * b + a] = (j0 + b) * nx + i0 + a;
-                    P.p_w[16 * p + 4 * b + a] = lag(0, 3, a, xi) * lag(0, 3, b, eta);
+                    P.p_w[16 * p + 4 * b + a] = (double)(lag(0, 3, a, xi) * lag(0, 3, b, eta));
                 }
         } else {
             const int i = (int)std::floor(fx + 0.5), j = (int)std::floor(fy + 0.5);
