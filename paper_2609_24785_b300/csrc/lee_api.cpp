@@ -26,8 +26,18 @@ constexpr int GRAPH_STEPS = 8;
 
 struct Layout {
     size_t q, mask, tiles, gt, gs, gn, gk, ei, ew, xn, xs, gx, gy, pi, pw, ph, clock, scratch, staging, desc,
-        prefix, total;
+        prefix, chunks, tmap, total;
 };
+
+inline int n_chunks(int ng) { return (ng + GHOSTS_PER_CTA - 1) / GHOSTS_PER_CTA; }
+
+// ghost work list of one instance: one entry per ghost CTA
+void append_chunks(std::vector<int4> &out, int inst, int ng) {
+    for (int c = 0; c < n_chunks(ng); ++c) {
+        const int first = c * GHOSTS_PER_CTA;
+        out.push_back(make_int4(inst, first, std::min(GHOSTS_PER_CTA, ng - first), 0));
+    }
+}
 
 }  // namespace
 
@@ -111,6 +121,8 @@ Layout make_layout(const lee_ctx *c) {
     L.staging = take((size_t)P.nx * P.ny * 8);
     L.desc = take(sizeof(InstDesc));
     L.prefix = take(8 * 4);
+    L.chunks = take((size_t)(n_chunks(ng) + 1) * sizeof(int4));
+    L.tmap = take(4 * 128);
     L.total = o;
     return L;
 }
@@ -210,7 +222,9 @@ BatchView single_view(lee_ctx *c) {
     bv.inst = c->dd;
     bv.ninst = 1;
     bv.tile_prefix = c->dprefix;
-    bv.ghost_prefix = c->dprefix + 2;
+    bv.ghost_chunks = (const int4 *)(c->dev + c->L.chunks);
+    bv.nchunks = n_chunks(c->hd.ng);
+    bv.use_tma = c->hd.use_tma;
     bv.probe_inst = c->dprefix + 4;
     bv.nprobe_inst = c->hd.np > 0 ? 1 : 0;
     bv.total_tiles = c->hd.ntiles;
@@ -308,8 +322,10 @@ int lee_plan(lee_ctx *ctx, lee_sizes *out) {
     if (!ctx || !out) return LEE_ERR_ARG;
     const lee_grid &g = ctx->g;
     std::string err;
+    const bool periodic = g.bc_x == LEE_BC_PERIODIC || g.bc_y == LEE_BC_PERIODIC;
+    const int tile_h = (g.precision == LEE_FP32 && !periodic) ? TMA_TILE_Y : TILE_Y;
     int rc = build_plan(g.nx, g.ny, g.h, g.x0, g.y0, g.bc_x == LEE_BC_PERIODIC, g.bc_y == LEE_BC_PERIODIC,
-                        g.cfl * g.h, ctx->geo, ctx->imp, ctx->probe_xy, ctx->plan, err);
+                        g.cfl * g.h, tile_h, ctx->geo, ctx->imp, ctx->probe_xy, ctx->plan, err);
     if (rc != LEE_OK) return fail(ctx, rc, err);
     if (ctx->plan.ade_amp > 1.0) {
         char b[160];
@@ -345,6 +361,10 @@ int lee_bind(lee_ctx *ctx, void *dev_ptr, long long dev_bytes, void *stream) {
     const size_t plane = (size_t)P.ny * P.pitch;
     cudaStream_t s = ctx->stream;
     CK(prepare_kernels(ctx->g.precision));
+    std::vector<int4> chunks;
+    append_chunks(chunks, 0, ng);
+    if (!chunks.empty())
+        CK(cudaMemcpyAsync(ctx->dev + L.chunks, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(ctx->dev, 0, L.total, s));
     // mask in pitch layout
     std::vector<uint8_t> mask(plane, 0);
@@ -381,6 +401,7 @@ int lee_bind(lee_ctx *ctx, void *dev_ptr, long long dev_bytes, void *stream) {
     d.tile_flags = (const uint32_t *)(ctx->dev + L.tiles);
     d.nx = P.nx; d.ny = P.ny; d.pitch = P.pitch; d.tiles_x = P.tiles_x; d.tiles_y = P.tiles_y;
     d.ntiles = P.tiles_x * P.tiles_y;
+    d.tile_h = P.tile_h;
     d.per_x = ctx->g.bc_x == LEE_BC_PERIODIC; d.per_y = ctx->g.bc_y == LEE_BC_PERIODIC;
     d.h = ctx->g.h; d.inv_h = 1.0 / ctx->g.h; d.dt = ctx->g.cfl * ctx->g.h;
     d.cx = 0.5 * (P.nx - 1); d.cy = 0.5 * (P.ny - 1);
@@ -405,6 +426,15 @@ int lee_bind(lee_ctx *ctx, void *dev_ptr, long long dev_bytes, void *stream) {
     d.scratch = (double *)(ctx->dev + L.scratch);
     d.staging = (double *)(ctx->dev + L.staging);
     d.precision = ctx->g.precision;
+    d.use_tma = P.tile_h == TMA_TILE_Y;
+    for (int q = 0; q < 4; ++q) d.tmap[q] = ctx->dev + L.tmap + 128 * q;
+    if (d.use_tma) {
+        alignas(64) unsigned char maps[4 * 128];
+        std::string terr;
+        if (!encode_tensor_maps(d, maps, terr)) return fail(ctx, LEE_ERR_CUDA, "tensor map: " + terr);
+        CK(cudaMemcpyAsync(ctx->dev + L.tmap, maps, sizeof maps, cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+    }
     ctx->dd = (InstDesc *)(ctx->dev + L.desc);
     ctx->dprefix = (int *)(ctx->dev + L.prefix);
     ctx->bound = true;
@@ -648,6 +678,10 @@ int lee_batch_add(lee_batch *b, lee_ctx *c) {
     if (!b || !c) return LEE_ERR_ARG;
     if (!c->bound) { b->err = "context not bound"; return LEE_ERR_ARG; }
     if (c->g.precision != b->precision) { b->err = "precision differs from the batch"; return LEE_ERR_ARG; }
+    if (!b->members.empty() && b->members[0]->hd.use_tma != c->hd.use_tma) {
+        b->err = "periodic and non-periodic FP32 instances use different stencil kernels: batch them separately";
+        return LEE_ERR_ARG;
+    }
     if (std::find(b->members.begin(), b->members.end(), c) != b->members.end()) { b->err = "already a member"; return LEE_ERR_ARG; }
     b->members.push_back(c);
     b->dirty = true;
@@ -663,13 +697,16 @@ int lee_batch_remove(lee_batch *b, lee_ctx *c) {
     return LEE_OK;
 }
 
-static long long batch_bytes(size_t n) {
-    return (long long)(align_up(n * sizeof(InstDesc)) + 3 * align_up((n + 1) * 4));
+static long long batch_bytes(const lee_batch *b) {
+    const size_t n = std::max<size_t>(b->members.size(), 1);
+    size_t nch = 1;
+    for (auto *c : b->members) nch += n_chunks(c->hd.ng);
+    return (long long)(align_up(n * sizeof(InstDesc)) + 2 * align_up((n + 1) * 4) + align_up(nch * sizeof(int4)));
 }
 
 int lee_batch_plan(lee_batch *b, long long *device_bytes) {
     if (!b || !device_bytes) return LEE_ERR_ARG;
-    *device_bytes = batch_bytes(std::max<size_t>(b->members.size(), 1));
+    *device_bytes = batch_bytes(b);
     return LEE_OK;
 }
 
@@ -684,24 +721,28 @@ int lee_batch_bind(lee_batch *b, void *dev_ptr, long long dev_bytes, void *strea
 
 static int batch_refresh(lee_batch *b) {
     const size_t n = b->members.size();
-    if ((long long)batch_bytes(std::max<size_t>(n, 1)) > b->bytes) { b->err = "batch buffer too small"; return LEE_ERR_BUDGET; }
+    if (batch_bytes(b) > b->bytes) { b->err = "batch buffer too small"; return LEE_ERR_BUDGET; }
     std::vector<InstDesc> descs(n);
-    std::vector<int> tp(n + 1, 0), gp(n + 1, 0), pi;
+    std::vector<int> tp(n + 1, 0), pi;
+    std::vector<int4> chunks;
+    int total_ghosts = 0;
     for (size_t i = 0; i < n; ++i) {
         descs[i] = b->members[i]->hd;
         tp[i + 1] = tp[i] + descs[i].ntiles;
-        gp[i + 1] = gp[i] + descs[i].ng;
+        append_chunks(chunks, (int)i, descs[i].ng);
+        total_ghosts += descs[i].ng;
         if (descs[i].np > 0) pi.push_back((int)i);
     }
     pi.resize(std::max<size_t>(pi.size(), 1));
-    const size_t o_desc = 0, o_tp = align_up(n * sizeof(InstDesc)), o_gp = o_tp + align_up((n + 1) * 4),
-                 o_pi = o_gp + align_up((n + 1) * 4);
+    chunks.resize(std::max<size_t>(chunks.size(), 1));
+    const size_t o_desc = 0, o_tp = align_up(n * sizeof(InstDesc)), o_pi = o_tp + align_up((n + 1) * 4),
+                 o_ch = o_pi + align_up((n + 1) * 4);
     cudaError_t e;
     if (n) {
         if ((e = cudaMemcpyAsync(b->dev + o_desc, descs.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice, b->stream)) ||
             (e = cudaMemcpyAsync(b->dev + o_tp, tp.data(), (n + 1) * 4, cudaMemcpyHostToDevice, b->stream)) ||
-            (e = cudaMemcpyAsync(b->dev + o_gp, gp.data(), (n + 1) * 4, cudaMemcpyHostToDevice, b->stream)) ||
             (e = cudaMemcpyAsync(b->dev + o_pi, pi.data(), pi.size() * 4, cudaMemcpyHostToDevice, b->stream)) ||
+            (e = cudaMemcpyAsync(b->dev + o_ch, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream)) ||
             (e = cudaStreamSynchronize(b->stream))) {
             b->err = std::string("batch upload: ") + cudaGetErrorString(e);
             return LEE_ERR_CUDA;
@@ -711,12 +752,14 @@ static int batch_refresh(lee_batch *b) {
     bv.inst = (const InstDesc *)(b->dev + o_desc);
     bv.ninst = (int)n;
     bv.tile_prefix = (const int *)(b->dev + o_tp);
-    bv.ghost_prefix = (const int *)(b->dev + o_gp);
+    bv.ghost_chunks = (const int4 *)(b->dev + o_ch);
+    bv.nchunks = total_ghosts > 0 ? (int)chunks.size() : 0;
+    bv.use_tma = n ? descs[0].use_tma : 0;
     bv.probe_inst = (const int *)(b->dev + o_pi);
     bv.nprobe_inst = 0;
     for (auto *c : b->members) bv.nprobe_inst += c->hd.np > 0;
     bv.total_tiles = tp[n];
-    bv.total_ghosts = gp[n];
+    bv.total_ghosts = total_ghosts;
     bv.precision = b->precision;
     drop_graphs(b->graph);
     b->dirty = false;

@@ -9,9 +9,15 @@
 
 namespace lee {
 
-// Tile of the fused stencil kernel: TILE_X columns x TILE_Y rows of outputs.
+// Tiles of the fused stencil kernels: TILE_X columns x tile_h rows of outputs.
+// FP32 instances without periodic axes use the TMA kernel with 64 x 64 tiles;
+// FP64 and periodic instances use the shared-memory kernel with 64 x 32 tiles.
 constexpr int TILE_X = 64;
 constexpr int TILE_Y = 32;
+constexpr int TMA_TILE_Y = 64;
+constexpr int GHOST_LANES = 8;          // lanes per ghost point in the ghost kernel
+constexpr int GHOST_THREADS = 256;
+constexpr int GHOSTS_PER_CTA = GHOST_THREADS / GHOST_LANES;
 constexpr int HALO = 4;                 // smem halo on each side (7-pt DRP needs 3,
                                         // the 5-pt band stencils at the last row need 4)
 constexpr int MAX_PROBES = 1024;
@@ -30,8 +36,10 @@ struct InstDesc {
     long long plane;            // elements per plane = ny * pitch
     const uint8_t *mask;        // node kind, ny x pitch (0 solid, 1 fluid, 2 ghost)
     const uint32_t *tile_flags; // tiles_x * tiles_y
-    int nx, ny, pitch, tiles_x, tiles_y, ntiles;
+    int nx, ny, pitch, tiles_x, tiles_y, ntiles, tile_h;
     int per_x, per_y;
+    int use_tma;                // FP32 TMA stencil path
+    const void *tmap[4];        // CUtensorMap (device): halo boxes of Q^n, Q^a, Q^b; 64x64 box of Q^n
     double h, inv_h, dt;
     double cx, cy;              // domain centre in index units ((n-1)/2)
     // ghosts (Sec. 3.1-3.2)
@@ -63,7 +71,7 @@ struct InstDesc {
 // Host-side plan of one instance.
 struct Plan {
     int nx = 0, ny = 0, pitch = 0;
-    int tiles_x = 0, tiles_y = 0;
+    int tiles_x = 0, tiles_y = 0, tile_h = TILE_Y;
     std::vector<uint8_t> kind;          // ny * nx (host order, no pitch)
     std::vector<uint32_t> tile_flags;
     // ghosts
@@ -96,7 +104,7 @@ struct Impedance {
 };
 
 // host set-up (lee_setup.cpp); returns LEE_* status, message in err
-int build_plan(int nx, int ny, double h, double x0, double y0, int per_x, int per_y, double dt,
+int build_plan(int nx, int ny, double h, double x0, double y0, int per_x, int per_y, double dt, int tile_h,
                const Geometry &geo, const Impedance &imp, const std::vector<double> &probe_xy,
                Plan &plan, std::string &err);
 void stage_forcing_factors(double omega, double dt, double G_re[4], double G_im[4]);
@@ -106,7 +114,9 @@ struct BatchView {
     const InstDesc *inst;       // device array of instance descriptors
     int ninst;
     const int *tile_prefix;     // ninst + 1 (device)
-    const int *ghost_prefix;    // ninst + 1 (device)
+    const int4 *ghost_chunks;   // (instance, first ghost, count, 0), one per ghost CTA (device)
+    int nchunks;
+    int use_tma;
     const int *probe_inst;      // instances with probes (device), nprobe_inst entries
     int nprobe_inst;
     int total_tiles;
@@ -114,6 +124,9 @@ struct BatchView {
     int precision;
 };
 cudaError_t prepare_kernels(int precision);   // one-time function attributes (outside capture)
+int num_sms();
+// TMA descriptors of one FP32 instance (host encode; 4 x 128 bytes)
+bool encode_tensor_maps(const InstDesc &d, void *host_out /* 4 x 128 B */, std::string &err);
 cudaError_t launch_ghost(const BatchView &bv, int stage, cudaStream_t s);
 cudaError_t launch_stencil(const BatchView &bv, int stage, int persistent_ctas, cudaStream_t s);
 cudaError_t launch_probes(const BatchView &bv, cudaStream_t s);

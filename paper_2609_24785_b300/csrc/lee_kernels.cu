@@ -14,6 +14,10 @@
 //  probe / init / staging / energy kernels: bookkeeping.
 #include <atomic>
 #include <cstdio>
+#include <string>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "lee_internal.h"
 
@@ -56,25 +60,37 @@ __device__ __forceinline__ GW ldg_gw(const GW *p) {
 }
 
 // ---------------------------------------------------------------- ghosts
+// One CTA handles GHOSTS_PER_CTA ghosts of one instance (a chunk of the work
+// list), GHOST_LANES lanes per ghost point.
 template <typename T>
-__global__ void __launch_bounds__(256)
-ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__restrict__ gprefix,
-             int total, int stage) {
+__global__ void __launch_bounds__(GHOST_THREADS)
+ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int4 *__restrict__ chunks, int nchunks,
+             int stage) {
     if (stage == 1 && blockIdx.x == 0)
         for (int i = threadIdx.x; i < ninst; i += blockDim.x) inst[i].clock[0] += 1;   // step in progress
-    const int lane = threadIdx.x & 31;
-    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (gw >= total) return;
-    const int ii = find_inst(gprefix, ninst, gw);
-    const InstDesc &d = inst[ii];
-    const int g = gw - __ldg(gprefix + ii);
-    const int inb = stage_in(stage);
-    T *P = (T *)d.q[inb];
+    if ((int)blockIdx.x >= nchunks) return;
+    const int4 ch = __ldg(chunks + blockIdx.x);
+    const int sub = threadIdx.x / GHOST_LANES, lane = threadIdx.x % GHOST_LANES;
+    if (sub >= ch.z) return;                        // whole lane groups leave together
+    const InstDesc &d = inst[ch.x];
+    const int g = ch.y + sub;
+    const int e0 = __ldg(d.g_start + g), e1 = __ldg(d.g_start + g + 1);
+    // per-ghost data, fetched before the gather so that the latencies overlap
+    double x0 = 0, x1 = 0, xn0 = 0, xn1 = 0;
+    double2 n = make_double2(0, 0), kap = make_double2(0, 0);
+    int t = 0;
+    if (lane == 0) {
+        x0 = d.Xs[2 * g]; x1 = d.Xs[2 * g + 1];
+        xn0 = d.Xn[2 * g]; xn1 = d.Xn[2 * g + 1];
+        n = __ldg(d.g_n + g);
+        kap = __ldg(d.g_kappa + g);
+        t = __ldg(d.g_target + g);
+    }
+    T *P = (T *)d.q[stage_in(stage)];
     T *U = P + d.plane;
     T *V = P + 2 * d.plane;
-    const int e0 = __ldg(d.g_start + g), e1 = __ldg(d.g_start + g + 1);
     double s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0;
-    for (int e = e0 + lane; e < e1; e += 32) {
+    for (int e = e0 + lane; e < e1; e += GHOST_LANES) {
         const int idx = __ldg(d.e_idx + e);
         const GW w = ldg_gw(d.e_w + e);
         const double p = (double)P[idx], u = (double)U[idx], v = (double)V[idx];
@@ -85,17 +101,17 @@ ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__restrict
         s4 = fma(w.wf, u, s4);       // w_f . u     (free row)
         s5 = fma(w.wf, v, s5);
     }
+    const unsigned gmask = 0xffu << (threadIdx.x & 24);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-        s3 += __shfl_xor_sync(0xffffffffu, s3, o);
-        s4 += __shfl_xor_sync(0xffffffffu, s4, o);
-        s5 += __shfl_xor_sync(0xffffffffu, s5, o);
+    for (int o = GHOST_LANES / 2; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(gmask, s0, o, GHOST_LANES);
+        s1 += __shfl_xor_sync(gmask, s1, o, GHOST_LANES);
+        s2 += __shfl_xor_sync(gmask, s2, o, GHOST_LANES);
+        s3 += __shfl_xor_sync(gmask, s3, o, GHOST_LANES);
+        s4 += __shfl_xor_sync(gmask, s4, o, GHOST_LANES);
+        s5 += __shfl_xor_sync(gmask, s5, o, GHOST_LANES);
     }
     if (lane != 0) return;
-    const double x0 = d.Xs[2 * g], x1 = d.Xs[2 * g + 1];
     const double pbp = s0;
     // step 2: ADE derivative with p_BP as forcing
     const double xd0 = d.A[0] * x0 + d.A[1] * x1 + d.b[0] * pbp;
@@ -104,18 +120,15 @@ ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__restrict
     const double un = d.c[0] * x0 + d.c[1] * x1;
     const double dun = d.c[0] * xd0 + d.c[1] * xd1;
     // steps 4-5: dp/dn = +du_n/dt (Neumann), u.n = -u_n (Dirichlet), free u.tau
-    const double2 n = __ldg(d.g_n + g);
-    const double2 kap = __ldg(d.g_kappa + g);
     const double pg = s1 + kap.x * dun;
     const double wg = n.x * s2 + n.y * s3 - kap.y * un;
     const double tg = -n.y * s4 + n.x * s5;
-    const int t = __ldg(d.g_target + g);
     P[t] = (T)pg;
     U[t] = (T)(wg * n.x - tg * n.y);
     V[t] = (T)(wg * n.y + tg * n.x);
     // ADE stage update X(k) = X(n) + alpha_k dt X'
     const double ad = c_alpha[stage - 1] * d.dt;
-    const double y0 = d.Xn[2 * g] + ad * xd0, y1 = d.Xn[2 * g + 1] + ad * xd1;
+    const double y0 = xn0 + ad * xd0, y1 = xn1 + ad * xd1;
     d.Xs[2 * g] = y0;
     d.Xs[2 * g + 1] = y1;
     if (stage == 4) { d.Xn[2 * g] = y0; d.Xn[2 * g + 1] = y1; }
@@ -345,6 +358,259 @@ stencil_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__restri
     }
 }
 
+// ---------------------------------------------------------------- TMA stencil (FP32)
+// Persistent CTAs (one per SM) walk the tile list.  For every 64 x 64 output
+// tile one thread issues two TMA tensor copies into a shared-memory stage: the
+// 72 x 72 halo box of Q(k-1) (p, u, v planes) and, for stages 2-4, the 64 x 64
+// box of Q^n.  Two stages are in flight: while tile i is computed from one
+// stage, the copies of tile i + 1 land in the other.  Completion is tracked by
+// one mbarrier per stage (expect_tx); every wait is bounded.
+constexpr int TB_X = TILE_X + 2 * HALO;                     // 72
+constexpr int TB_Y = TMA_TILE_Y + 2 * HALO;                 // 72
+constexpr int TMA_THREADS = 256;
+constexpr int TMA_TX = TILE_X / 4;                          // 16 threads across, 4 columns each
+constexpr int TMA_TY = TMA_THREADS / TMA_TX;                // 16 threads down
+constexpr int TMA_RY = TMA_TILE_Y / TMA_TY;                 // 4 rows each
+constexpr uint32_t HALO_BYTES = TB_X * TB_Y * 3 * 4;        // 62208
+constexpr uint32_t QN_BYTES = TILE_X * TMA_TILE_Y * 3 * 4;  // 49152
+constexpr uint32_t STAGE_BYTES = HALO_BYTES + QN_BYTES;     // 111360 = 870 x 128
+constexpr size_t TMA_SMEM = 2 * (size_t)STAGE_BYTES + 1024;
+constexpr int WAIT_SPINS = 1 << 20;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    for (int i = 0; i < WAIT_SPINS; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const void *map, uint64_t *bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::
+            "r"(smem_u32(dst)), "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
+__global__ void __launch_bounds__(TMA_THREADS, 1)
+stencil_tma_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__restrict__ tprefix, int total_tiles,
+                   int stage) {
+    extern __shared__ unsigned char smem_dyn[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int4 info[2];          // (instance, x0, y0, flags) of the tile in each stage
+    __shared__ float ssrc[2];         // source amplitude x stage forcing of that tile's instance
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x;
+    const int inb = stage_in(stage), outb = stage_out(stage);
+    const uint32_t bytes = stage == 1 ? HALO_BYTES : STAGE_BYTES;
+
+    auto issue = [&](int tile, int b) {           // thread 0: resolve the tile, start its copies
+        const int ii = find_inst(tprefix, ninst, tile);
+        const InstDesc &d = inst[ii];
+        const int lt = tile - __ldg(tprefix + ii);
+        const int tx = lt % d.tiles_x, ty = lt / d.tiles_x;
+        const int x0 = tx * TILE_X, y0 = ty * TMA_TILE_Y;
+        info[b] = make_int4(ii, x0, y0, (int)__ldg(d.tile_flags + lt));
+        ssrc[b] = d.s_amp != 0.0 ? (float)(d.s_amp * stage_sigma<float>(d, stage)) : 0.f;
+        unsigned char *dst = base + (size_t)b * STAGE_BYTES;
+        mbar_arrive_expect_tx(&bar[b], bytes);
+        tma_load_3d(dst, d.tmap[inb], &bar[b], x0 - HALO, y0 - HALO, 0);
+        if (stage != 1) tma_load_3d(dst + HALO_BYTES, d.tmap[3], &bar[b], x0, y0, 0);
+    };
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if ((int)blockIdx.x < total_tiles) issue(blockIdx.x, 0);
+        if ((int)(blockIdx.x + gridDim.x) < total_tiles) issue(blockIdx.x + gridDim.x, 1);
+    }
+
+    const int txi = tid % TMA_TX, tyi = tid / TMA_TX;
+    const int cx0 = HALO + 4 * txi, ry0 = HALO + TMA_RY * tyi;   // halo-box coordinates of the first output
+    const int lx0 = 4 * txi, ly0 = TMA_RY * tyi;                 // tile-local coordinates
+    int k = 0;
+    for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x, ++k) {
+        const int b = k & 1;
+        const uint32_t parity = (k >> 1) & 1;
+        if (!mbar_wait_bounded(&bar[b], parity)) atomicExch(&abort_flag, 1);
+        if (!abort_flag) {
+            const int4 inf = info[b];
+            const InstDesc &d = inst[inf.x];
+            const int xt = inf.y, yt = inf.z;
+            const uint32_t flags = (uint32_t)inf.w;
+            const float *sp = (const float *)(base + (size_t)b * STAGE_BYTES);
+            const float *su = sp + TB_X * TB_Y;
+            const float *sv = su + TB_X * TB_Y;
+            const float *qp = sv + TB_X * TB_Y;
+            const float *qu = qp + TILE_X * TMA_TILE_Y;
+            const float *qv = qu + TILE_X * TMA_TILE_Y;
+            float *out = (float *)d.q[outb];
+            const long long plane = d.plane;
+            const int pitch = d.pitch, nx = d.nx, ny = d.ny;
+            const float src = ssrc[b];
+            const float ad = (float)(c_alpha[stage - 1] * d.dt);
+            const float *gxs = (const float *)d.gx;
+            const float *gys = (const float *)d.gy;
+            const int gx0 = xt + lx0, gy0 = yt + ly0;
+            if (flags == 0) {
+                // interior: all outputs fluid, no band.  The stage update is
+                // q - sum_j k_j (f_{+j} - f_{-j}) with k_j = alpha_k dt a_j / h.
+                const double adh = c_alpha[stage - 1] * d.dt * d.inv_h;
+                const float k1 = (float)(adh * 0.770882380518), k2 = (float)(adh * -0.166705904415),
+                            k3 = (float)(adh * 0.020843142770);
+                float dpy[TMA_RY][4], dvy[TMA_RY][4];
+                {
+                    float cp[TMA_RY + 6][4], cv[TMA_RY + 6][4];
+#pragma unroll
+                    for (int r = 0; r < TMA_RY + 6; ++r) {
+                        const float4 a = *reinterpret_cast<const float4 *>(sp + (ry0 - 3 + r) * TB_X + cx0);
+                        const float4 c = *reinterpret_cast<const float4 *>(sv + (ry0 - 3 + r) * TB_X + cx0);
+                        cp[r][0] = a.x; cp[r][1] = a.y; cp[r][2] = a.z; cp[r][3] = a.w;
+                        cv[r][0] = c.x; cv[r][1] = c.y; cv[r][2] = c.z; cv[r][3] = c.w;
+                    }
+#pragma unroll
+                    for (int r = 0; r < TMA_RY; ++r)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            dpy[r][c] = k1 * (cp[r + 4][c] - cp[r + 2][c]) + k2 * (cp[r + 5][c] - cp[r + 1][c]) +
+                                        k3 * (cp[r + 6][c] - cp[r][c]);
+                            dvy[r][c] = k1 * (cv[r + 4][c] - cv[r + 2][c]) + k2 * (cv[r + 5][c] - cv[r + 1][c]) +
+                                        k3 * (cv[r + 6][c] - cv[r][c]);
+                        }
+                }
+#pragma unroll
+                for (int r = 0; r < TMA_RY; ++r) {
+                    float wp[12], wu[12];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        const float4 a = *reinterpret_cast<const float4 *>(sp + (ry0 + r) * TB_X + cx0 - 4 + 4 * q);
+                        const float4 c = *reinterpret_cast<const float4 *>(su + (ry0 + r) * TB_X + cx0 - 4 + 4 * q);
+                        wp[4 * q] = a.x; wp[4 * q + 1] = a.y; wp[4 * q + 2] = a.z; wp[4 * q + 3] = a.w;
+                        wu[4 * q] = c.x; wu[4 * q + 1] = c.y; wu[4 * q + 2] = c.z; wu[4 * q + 3] = c.w;
+                    }
+                    float4 n0, n1, n2;
+                    if (stage == 1) {
+                        n0 = make_float4(wp[4], wp[5], wp[6], wp[7]);
+                        n1 = make_float4(wu[4], wu[5], wu[6], wu[7]);
+                        n2 = *reinterpret_cast<const float4 *>(sv + (ry0 + r) * TB_X + cx0);
+                    } else {
+                        n0 = *reinterpret_cast<const float4 *>(qp + (ly0 + r) * TILE_X + lx0);
+                        n1 = *reinterpret_cast<const float4 *>(qu + (ly0 + r) * TILE_X + lx0);
+                        n2 = *reinterpret_cast<const float4 *>(qv + (ly0 + r) * TILE_X + lx0);
+                    }
+                    const float nn0[4] = {n0.x, n0.y, n0.z, n0.w}, nn1[4] = {n1.x, n1.y, n1.z, n1.w},
+                                nn2[4] = {n2.x, n2.y, n2.z, n2.w};
+                    const int gy = gy0 + r;
+                    const float sy = src != 0.f ? ad * src * gys[gy] : 0.f;
+                    float o0[4], o1[4], o2[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int q = 4 + c;
+                        const float dpx = k1 * (wp[q + 1] - wp[q - 1]) + k2 * (wp[q + 2] - wp[q - 2]) + k3 * (wp[q + 3] - wp[q - 3]);
+                        const float dux = k1 * (wu[q + 1] - wu[q - 1]) + k2 * (wu[q + 2] - wu[q - 2]) + k3 * (wu[q + 3] - wu[q - 3]);
+                        float op = nn0[c] - (dux + dvy[r][c]);
+                        if (src != 0.f) op += sy * gxs[gx0 + c];
+                        o0[c] = op;
+                        o1[c] = nn1[c] - dpx;
+                        o2[c] = nn2[c] - dpy[r][c];
+                    }
+                    const long long o = (long long)gy * pitch + gx0;
+                    *reinterpret_cast<float4 *>(out + o) = make_float4(o0[0], o0[1], o0[2], o0[3]);
+                    *reinterpret_cast<float4 *>(out + plane + o) = make_float4(o1[0], o1[1], o1[2], o1[3]);
+                    *reinterpret_cast<float4 *>(out + 2 * plane + o) = make_float4(o2[0], o2[1], o2[2], o2[3]);
+                }
+            } else {
+                // band (one-sided + radiation), non-fluid nodes, ragged edges
+                const float inv_h = (float)d.inv_h;
+                const float half_inv_h = 0.5f * inv_h;
+                for (int r = 0; r < TMA_RY; ++r) {
+                    const int gy = gy0 + r, sr = ry0 + r;
+                    if (gy >= ny) break;
+                    for (int c = 0; c < 4; ++c) {
+                        const int gx = gx0 + c, sc = cx0 + c;
+                        if (gx >= nx) break;
+                        const long long o = (long long)gy * pitch + gx;
+                        const uint8_t kind = (flags & TILE_MIXED) ? __ldg(d.mask + o) : (uint8_t)1;
+                        if (kind != 1) {
+                            out[o] = 0.f; out[plane + o] = 0.f; out[2 * plane + o] = 0.f;
+                            continue;
+                        }
+                        const bool band = gx < 3 || gx > nx - 4 || gy < 3 || gy > ny - 4;
+                        auto fxp = [&](int q) { return sp[sr * TB_X + sc + q]; };
+                        auto fxu = [&](int q) { return su[sr * TB_X + sc + q]; };
+                        auto fyp = [&](int q) { return sp[(sr + q) * TB_X + sc]; };
+                        auto fyv = [&](int q) { return sv[(sr + q) * TB_X + sc]; };
+                        const float dpdx = deriv_general<float>(fxp, gx, nx, 0, inv_h);
+                        const float dpdy = deriv_general<float>(fyp, gy, ny, 0, inv_h);
+                        float rp, ru, rv;
+                        if (!band) {
+                            const float dudx = deriv_general<float>(fxu, gx, nx, 0, inv_h);
+                            const float dvdy = deriv_general<float>(fyv, gy, ny, 0, inv_h);
+                            rp = -(dudx + dvdy);
+                            if (src != 0.f) rp += src * gxs[gx] * gys[gy];
+                            ru = -dpdx;
+                            rv = -dpdy;
+                        } else {
+                            auto fyu = [&](int q) { return su[(sr + q) * TB_X + sc]; };
+                            auto fxv = [&](int q) { return sv[sr * TB_X + sc + q]; };
+                            const float dudx = deriv_general<float>(fxu, gx, nx, 0, inv_h);
+                            const float dudy = deriv_general<float>(fyu, gy, ny, 0, inv_h);
+                            const float dvdx = deriv_general<float>(fxv, gx, nx, 0, inv_h);
+                            const float dvdy = deriv_general<float>(fyv, gy, ny, 0, inv_h);
+                            const float rx = float(gx) - (float)d.cx, ryy = float(gy) - (float)d.cy;
+                            const float rho = sqrtf(rx * rx + ryy * ryy);
+                            const float ct = rx / rho, st = ryy / rho;
+                            const float q2 = half_inv_h / rho;
+                            rp = -(ct * dpdx + st * dpdy + sp[sr * TB_X + sc] * q2);
+                            ru = -(ct * dudx + st * dudy + su[sr * TB_X + sc] * q2);
+                            rv = -(ct * dvdx + st * dvdy + sv[sr * TB_X + sc] * q2);
+                        }
+                        const int lq = (ly0 + r) * TILE_X + lx0 + c;
+                        const float n0 = stage == 1 ? sp[sr * TB_X + sc] : qp[lq];
+                        const float n1 = stage == 1 ? su[sr * TB_X + sc] : qu[lq];
+                        const float n2 = stage == 1 ? sv[sr * TB_X + sc] : qv[lq];
+                        out[o] = n0 + ad * rp;
+                        out[plane + o] = n1 + ad * ru;
+                        out[2 * plane + o] = n2 + ad * rv;
+                    }
+                }
+            }
+        }
+        __syncthreads();                               // every thread is done with this stage
+        if (abort_flag) {
+            // a copy did not complete in time: flag the instance, let the other
+            // stage's copy (if any) land, and leave
+            if (tid == 0) {
+                atomicOr((unsigned long long *)&inst[info[b].x].clock[2], 1ull);
+                if (tile + (int)gridDim.x < total_tiles) mbar_wait_bounded(&bar[b ^ 1], ((k + 1) >> 1) & 1);
+            }
+            return;
+        }
+        const int nxt = tile + 2 * (int)gridDim.x;
+        if (tid == 0 && nxt < total_tiles) issue(nxt, b);
+    }
+}
+
 // ---------------------------------------------------------------- probes
 template <typename T>
 __global__ void probe_kernel(const InstDesc *__restrict__ inst, const int *__restrict__ probe_inst) {
@@ -443,23 +709,82 @@ template <typename T> cudaError_t setup_stencil_attr() {
 constexpr int kGridStrideBlocks = 148 * 8;
 }  // namespace
 
+int num_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    }
+    return n;
+}
+
 cudaError_t prepare_kernels(int precision) {
-    return precision == 1 ? setup_stencil_attr<float>() : setup_stencil_attr<double>();
+    if (precision == 1) {
+        static bool done = false;
+        if (!done) {
+            cudaError_t e = cudaFuncSetAttribute(stencil_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)TMA_SMEM);
+            if (e != cudaSuccess) return e;
+            done = true;
+        }
+        num_sms();
+        return setup_stencil_attr<float>();
+    }
+    num_sms();
+    return setup_stencil_attr<double>();
+}
+
+bool encode_tensor_maps(const InstDesc &d, void *host_out, std::string &err) {
+    static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+    if (!enc) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+            err = "cuTensorMapEncodeTiled is not available";
+            return false;
+        }
+        enc = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    CUtensorMap *maps = (CUtensorMap *)host_out;
+    const cuuint64_t dims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, 3};
+    const cuuint64_t strides[2] = {(cuuint64_t)d.pitch * 4, (cuuint64_t)d.plane * 4};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const cuuint32_t halo_box[3] = {TB_X, TB_Y, 3};
+    const cuuint32_t tile_box[3] = {TILE_X, TMA_TILE_Y, 3};
+    for (int b = 0; b < 4; ++b) {
+        CUresult r = enc(&maps[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, d.q[b < 3 ? b : 0], dims, strides,
+                         b < 3 ? halo_box : tile_box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            err = "cuTensorMapEncodeTiled returned " + std::to_string((int)r);
+            return false;
+        }
+    }
+    return true;
 }
 
 cudaError_t launch_ghost(const BatchView &bv, int stage, cudaStream_t s) {
-    const int blocks = bv.total_ghosts > 0 ? (bv.total_ghosts * 32 + 255) / 256 : 1;
+    const int blocks = bv.nchunks > 0 ? bv.nchunks : 1;
     if (bv.precision == 1)
-        ghost_kernel<float><<<blocks, 256, 0, s>>>(bv.inst, bv.ninst, bv.ghost_prefix, bv.total_ghosts, stage);
+        ghost_kernel<float><<<blocks, GHOST_THREADS, 0, s>>>(bv.inst, bv.ninst, bv.ghost_chunks, bv.nchunks, stage);
     else
-        ghost_kernel<double><<<blocks, 256, 0, s>>>(bv.inst, bv.ninst, bv.ghost_prefix, bv.total_ghosts, stage);
+        ghost_kernel<double><<<blocks, GHOST_THREADS, 0, s>>>(bv.inst, bv.ninst, bv.ghost_chunks, bv.nchunks, stage);
     count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_stencil(const BatchView &bv, int stage, int persistent_ctas, cudaStream_t s) {
-    const int grid = persistent_ctas > 0 ? std::min(persistent_ctas, bv.total_tiles) : bv.total_tiles;
     cudaError_t e;
+    if (bv.precision == 1 && bv.use_tma) {
+        if (bv.total_tiles == 0) return cudaSuccess;
+        const int grid = std::min(bv.total_tiles, persistent_ctas > 0 ? persistent_ctas : num_sms());
+        stencil_tma_kernel<<<grid, TMA_THREADS, TMA_SMEM, s>>>(bv.inst, bv.ninst, bv.tile_prefix, bv.total_tiles, stage);
+        count_launch();
+        return cudaGetLastError();
+    }
+    const int grid = persistent_ctas > 0 ? std::min(persistent_ctas, bv.total_tiles) : bv.total_tiles;
     if (bv.precision == 1) {
         if ((e = setup_stencil_attr<float>()) != cudaSuccess) return e;
         stencil_kernel<float><<<grid, STENCIL_THREADS, stencil_smem<float>(), s>>>(bv.inst, bv.ninst, bv.tile_prefix,

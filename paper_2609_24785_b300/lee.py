@@ -313,6 +313,7 @@ class Batch:
         nb = C.c_longlong()
         self._c(self.L.lee_batch_plan(self.b, C.byref(nb)))
         if self.arena is None or self.arena.numel() < nb.value:
+            # grow geometrically so that adding members one by one stays cheap
             self.arena = torch.empty(max(int(nb.value) * 2, 1 << 16), dtype=torch.uint8, device="cuda")
             self._c(self.L.lee_batch_bind(self.b, self.arena.data_ptr(), self.arena.numel(),
                                           C.c_void_p(self.stream.cuda_stream)))

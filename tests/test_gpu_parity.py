@@ -14,10 +14,17 @@ from _helpers import make_oracle, make_solver, field_error, rel_l2
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-12, "fp32": 1e-5}
+# The 128^2 flat wall is specified in FP64 only.  FP32 storage by itself (the
+# FP64 oracle with its state rounded to FP32 after every stage) leaves a
+# relative L2 of 4.6e-5 there after 400 steps, because the pulse leaves the
+# domain and the remaining field is ~30x smaller than the initial one; its
+# FP32 run is checked against twice that floor.
+FLAT_FP32_TOL = 1e-4
 
 
-def _check(case, precision, steps=None, ade=True, probes=True):
+def _check(case, precision, steps=None, ade=True, probes=True, tol=None):
     steps = case.steps if steps is None else steps
+    tol = TOL[precision] if tol is None else tol
     s = make_solver(case, precision)
     o = make_oracle(case)
     s.step(steps)
@@ -25,27 +32,31 @@ def _check(case, precision, steps=None, ade=True, probes=True):
     o.run(steps)
     assert s.steps_done() == steps == o.step
     err = field_error(s, o)
-    assert err <= TOL[precision], (case.name, precision, err)
+    assert err <= tol, (case.name, precision, err)
     if ade and o.n_ghost and case.imp[0] == "msd":
         ea = rel_l2(s.ade(), o.ade())
-        assert ea <= TOL[precision], ("ade", ea)
+        assert ea <= tol, ("ade", ea)
     if probes and len(case.probes):
         ep = rel_l2(s.probes(), o.probes())
-        assert ep <= TOL[precision], ("probes", ep)
+        assert ep <= tol, ("probes", ep)
     return s, o, err
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_flat_wall_128_critical_ade(precision, cuda_device):
     """Inclined impedance wall, 128^2, R = 2 sqrt(KM) (double pole), 400 steps."""
-    _check(workloads.flat_wall(128), precision)
+    _check(workloads.flat_wall(128), precision, tol=FLAT_FP32_TOL if precision == "fp32" else None)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_cylinder_ragged_real_poles(precision, cuda_device):
     """Cylinder pulse on a ragged 200 x 136 grid (partial tiles in x and y),
-    two real poles (one stiff), 300 steps."""
+    radius 20 cells, pulse half-width 4 cells as in the 1024^2 workload, two
+    real poles (one stiff), 300 steps."""
     case = workloads.cylinder_pulse(256, nx=200, ny=136)
+    c = case.centre
+    case.wall = ("cyl", c[0], c[1], 20.3 * case.h)
+    case.init = ("pulse", c[0] + 40 * case.h, c[1] + 3 * case.h, 1.0, 4 * case.h)
     _check(case, precision, steps=300)
 
 
@@ -68,10 +79,13 @@ def test_rigid_cylinder_packet(cuda_device):
 def test_periodic_flat_wall(cuda_device):
     """Quasi-1D wall normal to x with periodic y (the App. A set-up)."""
     h = 0.01
+    # a packet at the wall resonance (k = 40 / 2 pi), stopped while it is on
+    # the wall so that the ADE states are large (after the reflection they
+    # decay to a rounding-level residue)
     case = workloads.Case("periodic", 330, 8, wall=("line", 300.5 * h, 0.0, math.pi / 2),
                           imp=("msd", 0.2, 0.025, 40.0),
-                          init=("packet", 230.5 * h, 0.0, 0.0, 2.0, 0.0, 1.0 / (6 * h)),
-                          probes=np.array([[265.5 * h, 3 * h]]), steps=300, periodic=(False, True))
+                          init=("packet", 240.5 * h, 0.0, 0.0, 2.0, 40.0 / (2 * math.pi), 1.0 / (12 * h)),
+                          probes=np.array([[265.5 * h, 3 * h]]), steps=130, periodic=(False, True))
     _check(case, "fp64")
 
 
@@ -145,10 +159,28 @@ def test_batch_equals_solo_and_oracle(cuda_device):
         assert field_error(m, o) <= TOL["fp64"]
 
 
+_ORACLE_CACHE = {}
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_full_size_cylinder_1024(precision, cuda_device):
-    """The 1024^2 cylinder-pulse workload at full size (the timed launch
-    configuration), compared over every node after 100 steps."""
+    """The 1024^2 cylinder-pulse workload at full size and its stated step
+    count (3000 steps, FP64 and FP32 bulk with FP64 ghosts), compared over
+    every fluid node, the ADE states and the probe ring."""
     case = workloads.cylinder_pulse(1024)
-    _check(case, precision, steps=100, probes=False)
+    steps = 3000
+    if "cyl1024" not in _ORACLE_CACHE:
+        o = make_oracle(case)
+        o.run(steps)
+        fluid = o.kind() == 1
+        _ORACLE_CACHE["cyl1024"] = (fluid, [o.field(f) for f in range(3)], o.ade(), o.probes())
+    fluid, fields, ade, probes = _ORACLE_CACHE["cyl1024"]
+    s = make_solver(case, precision)
+    s.step(steps)
+    s.sync()
+    err = rel_l2(np.concatenate([s.field(f)[fluid] for f in range(3)]), np.concatenate([fl[fluid] for fl in fields]))
+    print("cyl1024 %s field rel-L2 %.3e" % (precision, err))
+    assert err <= TOL[precision], err
+    assert rel_l2(s.ade(), ade) <= TOL[precision]
+    assert rel_l2(s.probes(), probes) <= TOL[precision]
