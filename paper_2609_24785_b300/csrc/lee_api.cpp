@@ -361,11 +361,11 @@ int lee_bind(lee_ctx *ctx, void *dev_ptr, long long dev_bytes, void *stream) {
     const size_t plane = (size_t)P.ny * P.pitch;
     cudaStream_t s = ctx->stream;
     CK(prepare_kernels(ctx->g.precision));
-    std::vector<int4> chunks;
+    CK(cudaMemsetAsync(ctx->dev, 0, L.total, s));
+    std::vector<int4> chunks;                 // ghost work list (after the memset above)
     append_chunks(chunks, 0, ng);
     if (!chunks.empty())
         CK(cudaMemcpyAsync(ctx->dev + L.chunks, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
-    CK(cudaMemsetAsync(ctx->dev, 0, L.total, s));
     // mask in pitch layout
     std::vector<uint8_t> mask(plane, 0);
     for (int j = 0; j < P.ny; ++j) std::memcpy(&mask[(size_t)j * P.pitch], &P.kind[(size_t)j * P.nx], P.nx);

@@ -135,17 +135,16 @@ ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int4 *__restric
 }
 
 // ---------------------------------------------------------------- stencil
-constexpr int SX = TILE_X + 2 * HALO;   // 72 smem columns
-constexpr int SY = TILE_Y + 2 * HALO;   // 40 smem rows
-constexpr int THREADS_X = TILE_X / 4;   // 16 threads across, 4 columns each
-constexpr int THREADS_Y = 8;
-constexpr int RY = TILE_Y / THREADS_Y;  // 4 rows per thread
-constexpr int STENCIL_THREADS = THREADS_X * THREADS_Y;
+// Shared-memory halo box: the tile's outputs plus HALO nodes on every side.
+constexpr int BOX_X = TILE_X + 2 * HALO;                    // 72
+constexpr int THREADS_X = TILE_X / 4;                       // 16 threads across, 4 columns each
+constexpr int RY = 4;                                       // rows per thread
+constexpr int LIST_CAP = 1024;                              // band points per tile (<= 3 (64 + 64))
 
 template <typename T> struct alignas(4 * sizeof(T)) Vec4 { T v[4]; };
 
 template <typename T>
-__device__ __forceinline__ Vec4<T> lds4(const T *p) { return *reinterpret_cast<const Vec4<T> *>(p); }
+__device__ __forceinline__ Vec4<T> ld4(const T *p) { return *reinterpret_cast<const Vec4<T> *>(p); }
 
 template <typename T>
 __device__ __forceinline__ T drp(T m3, T m2, T m1, T p1, T p2, T p3) {
@@ -166,7 +165,6 @@ __device__ __forceinline__ T deriv_general(F f, int x, int n, int per, T inv_h) 
     return (f(-2) - T(8) * f(-1) + T(8) * f(1) - f(2)) * i12;              // x == n - 3
 }
 
-template <typename T>
 __device__ __forceinline__ double stage_sigma(const InstDesc &d, int stage) {
     const double tn = (double)d.clock[0] * d.dt;
     double sn, cs;
@@ -174,15 +172,196 @@ __device__ __forceinline__ double stage_sigma(const InstDesc &d, int stage) {
     return sn * d.G_re[stage - 1] + cs * d.G_im[stage - 1];
 }
 
+// Where Q^n comes from: the halo box itself (stage 1), a shared-memory tile
+// box (TMA kernel) or global memory.  (x, y) are tile-local.
+template <typename T> struct QnSrc {
+    const T *p, *u, *v;
+    long long stride;
+    __device__ __forceinline__ long long at(int x, int y) const { return (long long)y * stride + x; }
+};
+
+// Step 6 of Sec. 3.2 on one tile: stage update of every output node owned by
+// this thread (4 columns x RY rows).  Interior fluid nodes take the vector
+// DRP path; non-fluid nodes get zeros; fluid nodes of the three outer layers
+// are appended to `list` and done afterwards by band_points().
+//   FOLD: FP32 form q - sum_j k_j (f_{+j} - f_{-j}), k_j = alpha dt a_j / h;
+//   else: q + alpha dt RHS with RHS from the DRP derivatives times 1/h.
+template <typename T, bool FOLD>
+__device__ __forceinline__ void tile_points(const T *sp, const T *su, const T *sv, const QnSrc<T> &qn,
+                                            const InstDesc &d, T *out, int xt, int yt, uint32_t flags, int stage,
+                                            T src, int txi, int tyi, unsigned short *list, int *list_n) {
+    const int cx0 = HALO + 4 * txi, ry0 = HALO + RY * tyi;     // box coordinates of the first output
+    const int lx0 = 4 * txi, ly0 = RY * tyi;                   // tile-local
+    const int gx0 = xt + lx0, gy0 = yt + ly0;
+    const int nx = d.nx, ny = d.ny, pitch = d.pitch;
+    const long long plane = d.plane;
+    const T ad = (T)(c_alpha[stage - 1] * d.dt);
+    const T inv_h = (T)d.inv_h;
+    const double adh = c_alpha[stage - 1] * d.dt * d.inv_h;
+    const T k1 = (T)(adh * 0.770882380518), k2 = (T)(adh * -0.166705904415), k3 = (T)(adh * 0.020843142770);
+    const T *gxs = (const T *)d.gx;
+    const T *gys = (const T *)d.gy;
+    if (gx0 >= nx || gy0 >= ny) return;
+
+    // y differences of p and v on the thread's 4 columns
+    T dpy[RY][4], dvy[RY][4];
+    {
+        T cp[RY + 6][4], cv[RY + 6][4];
+#pragma unroll
+        for (int r = 0; r < RY + 6; ++r) {
+            const Vec4<T> a = ld4(sp + (ry0 - 3 + r) * BOX_X + cx0);
+            const Vec4<T> c = ld4(sv + (ry0 - 3 + r) * BOX_X + cx0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) { cp[r][q] = a.v[q]; cv[r][q] = c.v[q]; }
+        }
+#pragma unroll
+        for (int r = 0; r < RY; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (FOLD) {
+                    dpy[r][q] = k1 * (cp[r + 4][q] - cp[r + 2][q]) + k2 * (cp[r + 5][q] - cp[r + 1][q]) +
+                                k3 * (cp[r + 6][q] - cp[r][q]);
+                    dvy[r][q] = k1 * (cv[r + 4][q] - cv[r + 2][q]) + k2 * (cv[r + 5][q] - cv[r + 1][q]) +
+                                k3 * (cv[r + 6][q] - cv[r][q]);
+                } else {
+                    dpy[r][q] = drp<T>(cp[r][q], cp[r + 1][q], cp[r + 2][q], cp[r + 4][q], cp[r + 5][q], cp[r + 6][q]) * inv_h;
+                    dvy[r][q] = drp<T>(cv[r][q], cv[r + 1][q], cv[r + 2][q], cv[r + 4][q], cv[r + 5][q], cv[r + 6][q]) * inv_h;
+                }
+            }
+    }
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+        const int gy = gy0 + r;
+        if (gy >= ny) break;
+        // node categories: 0 interior fluid, 1 non-fluid (zero), 2 band fluid (list), 3 outside
+        int cat[4] = {0, 0, 0, 0};
+        bool simple = true;
+        if (flags) {
+            uchar4 kind = make_uchar4(1, 1, 1, 1);
+            if (flags & TILE_MIXED) kind = *reinterpret_cast<const uchar4 *>(d.mask + (long long)gy * pitch + gx0);
+            const unsigned char kk[4] = {kind.x, kind.y, kind.z, kind.w};
+            const bool yband = !d.per_y && (gy < 3 || gy > ny - 4);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int gx = gx0 + q;
+                if (gx >= nx) cat[q] = 3;
+                else if (kk[q] != 1) cat[q] = 1;
+                else if (yband || (!d.per_x && (gx < 3 || gx > nx - 4))) cat[q] = 2;
+                simple = simple && cat[q] == 0;
+            }
+        }
+        T wp[12], wu[12];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const Vec4<T> a = ld4(sp + (ry0 + r) * BOX_X + cx0 - 4 + 4 * q);
+            const Vec4<T> c = ld4(su + (ry0 + r) * BOX_X + cx0 - 4 + 4 * q);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) { wp[4 * q + e] = a.v[e]; wu[4 * q + e] = c.v[e]; }
+        }
+        const Vec4<T> n0 = ld4(qn.p + qn.at(lx0, ly0 + r));
+        const Vec4<T> n1 = ld4(qn.u + qn.at(lx0, ly0 + r));
+        const Vec4<T> n2 = ld4(qn.v + qn.at(lx0, ly0 + r));
+        const T sy = src != T(0) ? src * gys[gy] : T(0);
+        Vec4<T> o0, o1, o2;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int c = 4 + q;
+            if (FOLD) {
+                const T dpx = k1 * (wp[c + 1] - wp[c - 1]) + k2 * (wp[c + 2] - wp[c - 2]) + k3 * (wp[c + 3] - wp[c - 3]);
+                const T dux = k1 * (wu[c + 1] - wu[c - 1]) + k2 * (wu[c + 2] - wu[c - 2]) + k3 * (wu[c + 3] - wu[c - 3]);
+                T op = n0.v[q] - (dux + dvy[r][q]);
+                if (src != T(0)) op += ad * sy * gxs[gx0 + q];
+                o0.v[q] = op;
+                o1.v[q] = n1.v[q] - dpx;
+                o2.v[q] = n2.v[q] - dpy[r][q];
+            } else {
+                const T dpdx = drp<T>(wp[c - 3], wp[c - 2], wp[c - 1], wp[c + 1], wp[c + 2], wp[c + 3]) * inv_h;
+                const T dudx = drp<T>(wu[c - 3], wu[c - 2], wu[c - 1], wu[c + 1], wu[c + 2], wu[c + 3]) * inv_h;
+                T rp = -(dudx + dvy[r][q]);
+                if (src != T(0)) rp += sy * gxs[gx0 + q];
+                o0.v[q] = n0.v[q] + ad * rp;
+                o1.v[q] = n1.v[q] + ad * (-dpdx);
+                o2.v[q] = n2.v[q] + ad * (-dpy[r][q]);
+            }
+        }
+        const long long o = (long long)gy * pitch + gx0;
+        if (simple) {
+            *reinterpret_cast<Vec4<T> *>(out + o) = o0;
+            *reinterpret_cast<Vec4<T> *>(out + plane + o) = o1;
+            *reinterpret_cast<Vec4<T> *>(out + 2 * plane + o) = o2;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (cat[q] == 0) {
+                    out[o + q] = o0.v[q]; out[plane + o + q] = o1.v[q]; out[2 * plane + o + q] = o2.v[q];
+                } else if (cat[q] == 1) {
+                    out[o + q] = T(0); out[plane + o + q] = T(0); out[2 * plane + o + q] = T(0);
+                } else if (cat[q] == 2) {
+                    const int slot = atomicAdd(list_n, 1);
+                    if (slot < LIST_CAP) list[slot] = (unsigned short)(((ly0 + r) << 8) | (lx0 + q));
+                }
+            }
+        }
+    }
+}
+
+// Fluid nodes of the three outer layers listed by tile_points(): one-sided
+// stencils (rows 0..2) and the radiation condition
+// dq/dt = -(cos th dq/dx + sin th dq/dy + q / (2 rho)), polar about the centre.
+template <typename T>
+__device__ __forceinline__ void band_points(const T *sp, const T *su, const T *sv, const QnSrc<T> &qn,
+                                            const InstDesc &d, T *out, int xt, int yt, int stage,
+                                            const unsigned short *list, int n, int tid, int nthreads) {
+    const T inv_h = (T)d.inv_h, half_inv_h = T(0.5) * inv_h;
+    const T ad = (T)(c_alpha[stage - 1] * d.dt);
+    const long long plane = d.plane;
+    for (int i = tid; i < n; i += nthreads) {
+        const int lx = list[i] & 0xff, ly = list[i] >> 8;
+        const int gx = xt + lx, gy = yt + ly;
+        const int sr = HALO + ly, sc = HALO + lx;
+        auto fxp = [&](int q) { return sp[sr * BOX_X + sc + q]; };
+        auto fxu = [&](int q) { return su[sr * BOX_X + sc + q]; };
+        auto fxv = [&](int q) { return sv[sr * BOX_X + sc + q]; };
+        auto fyp = [&](int q) { return sp[(sr + q) * BOX_X + sc]; };
+        auto fyu = [&](int q) { return su[(sr + q) * BOX_X + sc]; };
+        auto fyv = [&](int q) { return sv[(sr + q) * BOX_X + sc]; };
+        const T dpdx = deriv_general<T>(fxp, gx, d.nx, d.per_x, inv_h);
+        const T dpdy = deriv_general<T>(fyp, gy, d.ny, d.per_y, inv_h);
+        const T dudx = deriv_general<T>(fxu, gx, d.nx, d.per_x, inv_h);
+        const T dudy = deriv_general<T>(fyu, gy, d.ny, d.per_y, inv_h);
+        const T dvdx = deriv_general<T>(fxv, gx, d.nx, d.per_x, inv_h);
+        const T dvdy = deriv_general<T>(fyv, gy, d.ny, d.per_y, inv_h);
+        const T rx = T(gx) - (T)d.cx, ryy = T(gy) - (T)d.cy;
+        const T rho = sqrt(rx * rx + ryy * ryy);
+        const T ct = rx / rho, st = ryy / rho;
+        const T q2 = half_inv_h / rho;                               // 1 / (2 h rho)
+        const T rp = -(ct * dpdx + st * dpdy + sp[sr * BOX_X + sc] * q2);
+        const T ru = -(ct * dudx + st * dudy + su[sr * BOX_X + sc] * q2);
+        const T rv = -(ct * dvdx + st * dvdy + sv[sr * BOX_X + sc] * q2);
+        const long long o = (long long)gy * d.pitch + gx;
+        const long long oq = qn.at(lx, ly);
+        out[o] = qn.p[oq] + ad * rp;
+        out[plane + o] = qn.u[oq] + ad * ru;
+        out[2 * plane + o] = qn.v[oq] + ad * rv;
+    }
+}
+
+// ---- shared-memory kernel (FP64, periodic instances): 64 x 32 tiles,
+// threads load the halo box, Q^n is read from global memory
+constexpr int SY = TILE_Y + 2 * HALO;                       // 40 box rows
+constexpr int STENCIL_THREADS = THREADS_X * (TILE_Y / RY);  // 128
+
 template <typename T>
 __global__ void __launch_bounds__(STENCIL_THREADS)
 stencil_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__restrict__ tprefix,
                int total_tiles, int stage) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    T (*sp)[SX] = reinterpret_cast<T (*)[SX]>(smem_raw);
-    T (*su)[SX] = sp + SY;
-    T (*sv)[SX] = su + SY;
+    T *sp = reinterpret_cast<T *>(smem_raw);
+    T *su = sp + SY * BOX_X;
+    T *sv = su + SY * BOX_X;
     __shared__ T s_src;
+    __shared__ unsigned short list[LIST_CAP];
+    __shared__ int list_n;
     const int inb = stage_in(stage), outb = stage_out(stage);
     const int txi = threadIdx.x % THREADS_X, tyi = threadIdx.x / THREADS_X;
 
@@ -197,8 +376,8 @@ stencil_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__restri
         const long long plane = d.plane;
         const int pitch = d.pitch, nx = d.nx, ny = d.ny;
 
-        // ---- halo tile of Q(k-1) into shared memory
-        constexpr int C4 = SX / 4;
+        // ---- halo box of Q(k-1) into shared memory
+        constexpr int C4 = BOX_X / 4;
         for (int e = threadIdx.x; e < SY * C4; e += STENCIL_THREADS) {
             const int r = e / C4, c = (e - r * C4) * 4;
             int gy = yt - HALO + r;
@@ -223,136 +402,28 @@ stencil_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__restri
             } else {
                 for (int q = 0; q < 4; ++q) vp.v[q] = vu.v[q] = vv.v[q] = T(0);
             }
-            *reinterpret_cast<Vec4<T> *>(&sp[r][c]) = vp;
-            *reinterpret_cast<Vec4<T> *>(&su[r][c]) = vu;
-            *reinterpret_cast<Vec4<T> *>(&sv[r][c]) = vv;
+            *reinterpret_cast<Vec4<T> *>(sp + r * BOX_X + c) = vp;
+            *reinterpret_cast<Vec4<T> *>(su + r * BOX_X + c) = vu;
+            *reinterpret_cast<Vec4<T> *>(sv + r * BOX_X + c) = vv;
         }
-        if (threadIdx.x == 0) s_src = d.s_amp != 0.0 ? (T)(d.s_amp * stage_sigma<T>(d, stage)) : T(0);
+        if (threadIdx.x == 0) {
+            s_src = d.s_amp != 0.0 ? (T)(d.s_amp * stage_sigma(d, stage)) : T(0);
+            list_n = 0;
+        }
         __syncthreads();
-
-        const T inv_h = (T)d.inv_h;
-        const T ad = (T)(c_alpha[stage - 1] * d.dt);
-        const T src = s_src;
-        const T *gxs = (const T *)d.gx;
-        const T *gys = (const T *)d.gy;
-        T *out = (T *)d.q[outb];
-        const T *qn = (const T *)d.q[0];
-        const int cx0 = HALO + 4 * txi;          // smem column of this thread's first output
-        const int ry0 = HALO + RY * tyi;         // smem row of this thread's first output
-        const int gx0 = xt + 4 * txi;
-        const int gy0 = yt + RY * tyi;
-
-        if (flags == 0) {
-            // ---- interior fast path: all outputs fluid, no band
-            T dpdy[RY][4], dvdy[RY][4];
-            {
-                T cp[RY + 6][4], cv[RY + 6][4];
-#pragma unroll
-                for (int r = 0; r < RY + 6; ++r) {
-                    const Vec4<T> a = lds4(&sp[ry0 - 3 + r][cx0]);
-                    const Vec4<T> b = lds4(&sv[ry0 - 3 + r][cx0]);
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) { cp[r][c] = a.v[c]; cv[r][c] = b.v[c]; }
-                }
-#pragma unroll
-                for (int r = 0; r < RY; ++r)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        dpdy[r][c] = drp<T>(cp[r][c], cp[r + 1][c], cp[r + 2][c], cp[r + 4][c], cp[r + 5][c], cp[r + 6][c]);
-                        dvdy[r][c] = drp<T>(cv[r][c], cv[r + 1][c], cv[r + 2][c], cv[r + 4][c], cv[r + 5][c], cv[r + 6][c]);
-                    }
-            }
-#pragma unroll
-            for (int r = 0; r < RY; ++r) {
-                T wp[12], wu[12];
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    const Vec4<T> a = lds4(&sp[ry0 + r][cx0 - 4 + 4 * q]);
-                    const Vec4<T> b = lds4(&su[ry0 + r][cx0 - 4 + 4 * q]);
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) { wp[4 * q + c] = a.v[c]; wu[4 * q + c] = b.v[c]; }
-                }
-                const int gy = gy0 + r;
-                const long long o = (long long)gy * pitch + gx0;
-                Vec4<T> n0, n1, n2;
-                if (stage == 1) {
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) { n0.v[c] = wp[4 + c]; n1.v[c] = wu[4 + c]; n2.v[c] = sv[ry0 + r][cx0 + c]; }
-                } else {
-                    n0 = *reinterpret_cast<const Vec4<T> *>(qn + o);
-                    n1 = *reinterpret_cast<const Vec4<T> *>(qn + plane + o);
-                    n2 = *reinterpret_cast<const Vec4<T> *>(qn + 2 * plane + o);
-                }
-                Vec4<T> o0, o1, o2;
-                const T gyv = src != T(0) ? gys[gy] : T(0);
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int k = 4 + c;
-                    const T dpdx = drp<T>(wp[k - 3], wp[k - 2], wp[k - 1], wp[k + 1], wp[k + 2], wp[k + 3]) * inv_h;
-                    const T dudx = drp<T>(wu[k - 3], wu[k - 2], wu[k - 1], wu[k + 1], wu[k + 2], wu[k + 3]) * inv_h;
-                    T rp = -(dudx + dvdy[r][c] * inv_h);
-                    if (src != T(0)) rp += src * gxs[gx0 + c] * gyv;
-                    o0.v[c] = n0.v[c] + ad * rp;
-                    o1.v[c] = n1.v[c] - ad * dpdx;
-                    o2.v[c] = n2.v[c] - ad * (dpdy[r][c] * inv_h);
-                }
-                *reinterpret_cast<Vec4<T> *>(out + o) = o0;
-                *reinterpret_cast<Vec4<T> *>(out + plane + o) = o1;
-                *reinterpret_cast<Vec4<T> *>(out + 2 * plane + o) = o2;
-            }
+        QnSrc<T> qn;
+        if (stage == 1) {
+            qn = QnSrc<T>{sp + HALO * BOX_X + HALO, su + HALO * BOX_X + HALO, sv + HALO * BOX_X + HALO, BOX_X};
         } else {
-            // ---- general path: band (one-sided + radiation), mask, ragged edges
-            const T half_inv_h = T(0.5) * inv_h;
-            for (int r = 0; r < RY; ++r) {
-                const int gy = gy0 + r, sr = ry0 + r;
-                if (gy >= ny) break;
-                for (int c = 0; c < 4; ++c) {
-                    const int gx = gx0 + c, sc = cx0 + c;
-                    if (gx >= nx) break;
-                    const long long o = (long long)gy * pitch + gx;
-                    const uint8_t kind = (flags & TILE_MIXED) ? __ldg(d.mask + o) : (uint8_t)1;
-                    if (kind != 1) {
-                        out[o] = T(0); out[plane + o] = T(0); out[2 * plane + o] = T(0);
-                        continue;
-                    }
-                    const bool band = (!d.per_x && (gx < 3 || gx > nx - 4)) || (!d.per_y && (gy < 3 || gy > ny - 4));
-                    auto fxp = [&](int k) { return sp[sr][sc + k]; };
-                    auto fxu = [&](int k) { return su[sr][sc + k]; };
-                    auto fyp = [&](int k) { return sp[sr + k][sc]; };
-                    auto fyv = [&](int k) { return sv[sr + k][sc]; };
-                    const T dpdx = deriv_general<T>(fxp, gx, nx, d.per_x, inv_h);
-                    const T dpdy = deriv_general<T>(fyp, gy, ny, d.per_y, inv_h);
-                    T rp, ru, rv;
-                    if (!band) {
-                        const T dudx = deriv_general<T>(fxu, gx, nx, d.per_x, inv_h);
-                        const T dvdy = deriv_general<T>(fyv, gy, ny, d.per_y, inv_h);
-                        rp = -(dudx + dvdy);
-                        if (src != T(0)) rp += src * gxs[gx] * gys[gy];
-                        ru = -dpdx;
-                        rv = -dpdy;
-                    } else {
-                        auto fyu = [&](int k) { return su[sr + k][sc]; };
-                        auto fxv = [&](int k) { return sv[sr][sc + k]; };
-                        const T dudx = deriv_general<T>(fxu, gx, nx, d.per_x, inv_h);
-                        const T dudy = deriv_general<T>(fyu, gy, ny, d.per_y, inv_h);
-                        const T dvdx = deriv_general<T>(fxv, gx, nx, d.per_x, inv_h);
-                        const T dvdy = deriv_general<T>(fyv, gy, ny, d.per_y, inv_h);
-                        const T rx = T(gx) - (T)d.cx, ryy = T(gy) - (T)d.cy;
-                        const T rho = sqrt(rx * rx + ryy * ryy);
-                        const T ct = rx / rho, st = ryy / rho;
-                        const T q2 = half_inv_h / rho;      // 1 / (2 h rho)
-                        rp = -(ct * dpdx + st * dpdy + sp[sr][sc] * q2);
-                        ru = -(ct * dudx + st * dudy + su[sr][sc] * q2);
-                        rv = -(ct * dvdx + st * dvdy + sv[sr][sc] * q2);
-                    }
-                    const T n0 = stage == 1 ? sp[sr][sc] : qn[o];
-                    const T n1 = stage == 1 ? su[sr][sc] : qn[plane + o];
-                    const T n2 = stage == 1 ? sv[sr][sc] : qn[2 * plane + o];
-                    out[o] = n0 + ad * rp;
-                    out[plane + o] = n1 + ad * ru;
-                    out[2 * plane + o] = n2 + ad * rv;
-                }
-            }
+            const T *q0 = (const T *)d.q[0] + (long long)yt * pitch + xt;
+            qn = QnSrc<T>{q0, q0 + plane, q0 + 2 * plane, pitch};
+        }
+        T *out = (T *)d.q[outb];
+        tile_points<T, false>(sp, su, sv, qn, d, out, xt, yt, flags, stage, s_src, txi, tyi, list, &list_n);
+        if (flags & TILE_BAND) {
+            __syncthreads();
+            band_points<T>(sp, su, sv, qn, d, out, xt, yt, stage, list, min(list_n, LIST_CAP), threadIdx.x,
+                           STENCIL_THREADS);
         }
         __syncthreads();
     }
@@ -365,13 +436,9 @@ stencil_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__restri
 // box of Q^n.  Two stages are in flight: while tile i is computed from one
 // stage, the copies of tile i + 1 land in the other.  Completion is tracked by
 // one mbarrier per stage (expect_tx); every wait is bounded.
-constexpr int TB_X = TILE_X + 2 * HALO;                     // 72
 constexpr int TB_Y = TMA_TILE_Y + 2 * HALO;                 // 72
-constexpr int TMA_THREADS = 256;
-constexpr int TMA_TX = TILE_X / 4;                          // 16 threads across, 4 columns each
-constexpr int TMA_TY = TMA_THREADS / TMA_TX;                // 16 threads down
-constexpr int TMA_RY = TMA_TILE_Y / TMA_TY;                 // 4 rows each
-constexpr uint32_t HALO_BYTES = TB_X * TB_Y * 3 * 4;        // 62208
+constexpr int TMA_THREADS = THREADS_X * (TMA_TILE_Y / RY);  // 256
+constexpr uint32_t HALO_BYTES = BOX_X * TB_Y * 3 * 4;       // 62208
 constexpr uint32_t QN_BYTES = TILE_X * TMA_TILE_Y * 3 * 4;  // 49152
 constexpr uint32_t STAGE_BYTES = HALO_BYTES + QN_BYTES;     // 111360 = 870 x 128
 constexpr size_t TMA_SMEM = 2 * (size_t)STAGE_BYTES + 1024;
@@ -414,6 +481,8 @@ stencil_tma_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__re
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int4 info[2];          // (instance, x0, y0, flags) of the tile in each stage
     __shared__ float ssrc[2];         // source amplitude x stage forcing of that tile's instance
+    __shared__ unsigned short list[LIST_CAP];
+    __shared__ int list_n[2];         // band-list counters, by tile parity
     __shared__ int abort_flag;
     const int tid = threadIdx.x;
     const int inb = stage_in(stage), outb = stage_out(stage);
@@ -426,7 +495,7 @@ stencil_tma_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__re
         const int tx = lt % d.tiles_x, ty = lt / d.tiles_x;
         const int x0 = tx * TILE_X, y0 = ty * TMA_TILE_Y;
         info[b] = make_int4(ii, x0, y0, (int)__ldg(d.tile_flags + lt));
-        ssrc[b] = d.s_amp != 0.0 ? (float)(d.s_amp * stage_sigma<float>(d, stage)) : 0.f;
+        ssrc[b] = d.s_amp != 0.0 ? (float)(d.s_amp * stage_sigma(d, stage)) : 0.f;
         unsigned char *dst = base + (size_t)b * STAGE_BYTES;
         mbar_arrive_expect_tx(&bar[b], bytes);
         tma_load_3d(dst, d.tmap[inb], &bar[b], x0 - HALO, y0 - HALO, 0);
@@ -437,6 +506,7 @@ stencil_tma_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__re
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         abort_flag = 0;
+        list_n[0] = list_n[1] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -445,155 +515,35 @@ stencil_tma_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__re
         if ((int)(blockIdx.x + gridDim.x) < total_tiles) issue(blockIdx.x + gridDim.x, 1);
     }
 
-    const int txi = tid % TMA_TX, tyi = tid / TMA_TX;
-    const int cx0 = HALO + 4 * txi, ry0 = HALO + TMA_RY * tyi;   // halo-box coordinates of the first output
-    const int lx0 = 4 * txi, ly0 = TMA_RY * tyi;                 // tile-local coordinates
+    const int txi = tid % THREADS_X, tyi = tid / THREADS_X;
     int k = 0;
     for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x, ++k) {
         const int b = k & 1;
         const uint32_t parity = (k >> 1) & 1;
         if (!mbar_wait_bounded(&bar[b], parity)) atomicExch(&abort_flag, 1);
+        // all threads are inside iteration k here: the counter of tile k + 1
+        // (last used by tile k - 1) can be cleared
+        if (tid == 0) list_n[b ^ 1] = 0;
+        const int4 inf = info[b];
         if (!abort_flag) {
-            const int4 inf = info[b];
             const InstDesc &d = inst[inf.x];
-            const int xt = inf.y, yt = inf.z;
-            const uint32_t flags = (uint32_t)inf.w;
             const float *sp = (const float *)(base + (size_t)b * STAGE_BYTES);
-            const float *su = sp + TB_X * TB_Y;
-            const float *sv = su + TB_X * TB_Y;
-            const float *qp = sv + TB_X * TB_Y;
-            const float *qu = qp + TILE_X * TMA_TILE_Y;
-            const float *qv = qu + TILE_X * TMA_TILE_Y;
-            float *out = (float *)d.q[outb];
-            const long long plane = d.plane;
-            const int pitch = d.pitch, nx = d.nx, ny = d.ny;
-            const float src = ssrc[b];
-            const float ad = (float)(c_alpha[stage - 1] * d.dt);
-            const float *gxs = (const float *)d.gx;
-            const float *gys = (const float *)d.gy;
-            const int gx0 = xt + lx0, gy0 = yt + ly0;
-            if (flags == 0) {
-                // interior: all outputs fluid, no band.  The stage update is
-                // q - sum_j k_j (f_{+j} - f_{-j}) with k_j = alpha_k dt a_j / h.
-                const double adh = c_alpha[stage - 1] * d.dt * d.inv_h;
-                const float k1 = (float)(adh * 0.770882380518), k2 = (float)(adh * -0.166705904415),
-                            k3 = (float)(adh * 0.020843142770);
-                float dpy[TMA_RY][4], dvy[TMA_RY][4];
-                {
-                    float cp[TMA_RY + 6][4], cv[TMA_RY + 6][4];
-#pragma unroll
-                    for (int r = 0; r < TMA_RY + 6; ++r) {
-                        const float4 a = *reinterpret_cast<const float4 *>(sp + (ry0 - 3 + r) * TB_X + cx0);
-                        const float4 c = *reinterpret_cast<const float4 *>(sv + (ry0 - 3 + r) * TB_X + cx0);
-                        cp[r][0] = a.x; cp[r][1] = a.y; cp[r][2] = a.z; cp[r][3] = a.w;
-                        cv[r][0] = c.x; cv[r][1] = c.y; cv[r][2] = c.z; cv[r][3] = c.w;
-                    }
-#pragma unroll
-                    for (int r = 0; r < TMA_RY; ++r)
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            dpy[r][c] = k1 * (cp[r + 4][c] - cp[r + 2][c]) + k2 * (cp[r + 5][c] - cp[r + 1][c]) +
-                                        k3 * (cp[r + 6][c] - cp[r][c]);
-                            dvy[r][c] = k1 * (cv[r + 4][c] - cv[r + 2][c]) + k2 * (cv[r + 5][c] - cv[r + 1][c]) +
-                                        k3 * (cv[r + 6][c] - cv[r][c]);
-                        }
-                }
-#pragma unroll
-                for (int r = 0; r < TMA_RY; ++r) {
-                    float wp[12], wu[12];
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        const float4 a = *reinterpret_cast<const float4 *>(sp + (ry0 + r) * TB_X + cx0 - 4 + 4 * q);
-                        const float4 c = *reinterpret_cast<const float4 *>(su + (ry0 + r) * TB_X + cx0 - 4 + 4 * q);
-                        wp[4 * q] = a.x; wp[4 * q + 1] = a.y; wp[4 * q + 2] = a.z; wp[4 * q + 3] = a.w;
-                        wu[4 * q] = c.x; wu[4 * q + 1] = c.y; wu[4 * q + 2] = c.z; wu[4 * q + 3] = c.w;
-                    }
-                    float4 n0, n1, n2;
-                    if (stage == 1) {
-                        n0 = make_float4(wp[4], wp[5], wp[6], wp[7]);
-                        n1 = make_float4(wu[4], wu[5], wu[6], wu[7]);
-                        n2 = *reinterpret_cast<const float4 *>(sv + (ry0 + r) * TB_X + cx0);
-                    } else {
-                        n0 = *reinterpret_cast<const float4 *>(qp + (ly0 + r) * TILE_X + lx0);
-                        n1 = *reinterpret_cast<const float4 *>(qu + (ly0 + r) * TILE_X + lx0);
-                        n2 = *reinterpret_cast<const float4 *>(qv + (ly0 + r) * TILE_X + lx0);
-                    }
-                    const float nn0[4] = {n0.x, n0.y, n0.z, n0.w}, nn1[4] = {n1.x, n1.y, n1.z, n1.w},
-                                nn2[4] = {n2.x, n2.y, n2.z, n2.w};
-                    const int gy = gy0 + r;
-                    const float sy = src != 0.f ? ad * src * gys[gy] : 0.f;
-                    float o0[4], o1[4], o2[4];
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const int q = 4 + c;
-                        const float dpx = k1 * (wp[q + 1] - wp[q - 1]) + k2 * (wp[q + 2] - wp[q - 2]) + k3 * (wp[q + 3] - wp[q - 3]);
-                        const float dux = k1 * (wu[q + 1] - wu[q - 1]) + k2 * (wu[q + 2] - wu[q - 2]) + k3 * (wu[q + 3] - wu[q - 3]);
-                        float op = nn0[c] - (dux + dvy[r][c]);
-                        if (src != 0.f) op += sy * gxs[gx0 + c];
-                        o0[c] = op;
-                        o1[c] = nn1[c] - dpx;
-                        o2[c] = nn2[c] - dpy[r][c];
-                    }
-                    const long long o = (long long)gy * pitch + gx0;
-                    *reinterpret_cast<float4 *>(out + o) = make_float4(o0[0], o0[1], o0[2], o0[3]);
-                    *reinterpret_cast<float4 *>(out + plane + o) = make_float4(o1[0], o1[1], o1[2], o1[3]);
-                    *reinterpret_cast<float4 *>(out + 2 * plane + o) = make_float4(o2[0], o2[1], o2[2], o2[3]);
-                }
+            const float *su = sp + BOX_X * TB_Y;
+            const float *sv = su + BOX_X * TB_Y;
+            QnSrc<float> qn;
+            if (stage == 1) {
+                qn = QnSrc<float>{sp + HALO * BOX_X + HALO, su + HALO * BOX_X + HALO, sv + HALO * BOX_X + HALO, BOX_X};
             } else {
-                // band (one-sided + radiation), non-fluid nodes, ragged edges
-                const float inv_h = (float)d.inv_h;
-                const float half_inv_h = 0.5f * inv_h;
-                for (int r = 0; r < TMA_RY; ++r) {
-                    const int gy = gy0 + r, sr = ry0 + r;
-                    if (gy >= ny) break;
-                    for (int c = 0; c < 4; ++c) {
-                        const int gx = gx0 + c, sc = cx0 + c;
-                        if (gx >= nx) break;
-                        const long long o = (long long)gy * pitch + gx;
-                        const uint8_t kind = (flags & TILE_MIXED) ? __ldg(d.mask + o) : (uint8_t)1;
-                        if (kind != 1) {
-                            out[o] = 0.f; out[plane + o] = 0.f; out[2 * plane + o] = 0.f;
-                            continue;
-                        }
-                        const bool band = gx < 3 || gx > nx - 4 || gy < 3 || gy > ny - 4;
-                        auto fxp = [&](int q) { return sp[sr * TB_X + sc + q]; };
-                        auto fxu = [&](int q) { return su[sr * TB_X + sc + q]; };
-                        auto fyp = [&](int q) { return sp[(sr + q) * TB_X + sc]; };
-                        auto fyv = [&](int q) { return sv[(sr + q) * TB_X + sc]; };
-                        const float dpdx = deriv_general<float>(fxp, gx, nx, 0, inv_h);
-                        const float dpdy = deriv_general<float>(fyp, gy, ny, 0, inv_h);
-                        float rp, ru, rv;
-                        if (!band) {
-                            const float dudx = deriv_general<float>(fxu, gx, nx, 0, inv_h);
-                            const float dvdy = deriv_general<float>(fyv, gy, ny, 0, inv_h);
-                            rp = -(dudx + dvdy);
-                            if (src != 0.f) rp += src * gxs[gx] * gys[gy];
-                            ru = -dpdx;
-                            rv = -dpdy;
-                        } else {
-                            auto fyu = [&](int q) { return su[(sr + q) * TB_X + sc]; };
-                            auto fxv = [&](int q) { return sv[sr * TB_X + sc + q]; };
-                            const float dudx = deriv_general<float>(fxu, gx, nx, 0, inv_h);
-                            const float dudy = deriv_general<float>(fyu, gy, ny, 0, inv_h);
-                            const float dvdx = deriv_general<float>(fxv, gx, nx, 0, inv_h);
-                            const float dvdy = deriv_general<float>(fyv, gy, ny, 0, inv_h);
-                            const float rx = float(gx) - (float)d.cx, ryy = float(gy) - (float)d.cy;
-                            const float rho = sqrtf(rx * rx + ryy * ryy);
-                            const float ct = rx / rho, st = ryy / rho;
-                            const float q2 = half_inv_h / rho;
-                            rp = -(ct * dpdx + st * dpdy + sp[sr * TB_X + sc] * q2);
-                            ru = -(ct * dudx + st * dudy + su[sr * TB_X + sc] * q2);
-                            rv = -(ct * dvdx + st * dvdy + sv[sr * TB_X + sc] * q2);
-                        }
-                        const int lq = (ly0 + r) * TILE_X + lx0 + c;
-                        const float n0 = stage == 1 ? sp[sr * TB_X + sc] : qp[lq];
-                        const float n1 = stage == 1 ? su[sr * TB_X + sc] : qu[lq];
-                        const float n2 = stage == 1 ? sv[sr * TB_X + sc] : qv[lq];
-                        out[o] = n0 + ad * rp;
-                        out[plane + o] = n1 + ad * ru;
-                        out[2 * plane + o] = n2 + ad * rv;
-                    }
-                }
+                const float *qp = sv + BOX_X * TB_Y;
+                qn = QnSrc<float>{qp, qp + TILE_X * TMA_TILE_Y, qp + 2 * TILE_X * TMA_TILE_Y, TILE_X};
+            }
+            float *out = (float *)d.q[outb];
+            tile_points<float, true>(sp, su, sv, qn, d, out, inf.y, inf.z, (uint32_t)inf.w, stage, ssrc[b], txi,
+                                     tyi, list, &list_n[b]);
+            if (inf.w & TILE_BAND) {
+                __syncthreads();
+                band_points<float>(sp, su, sv, qn, d, out, inf.y, inf.z, stage, list, min(list_n[b], LIST_CAP), tid,
+                                   TMA_THREADS);
             }
         }
         __syncthreads();                               // every thread is done with this stage
@@ -601,13 +551,15 @@ stencil_tma_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__re
             // a copy did not complete in time: flag the instance, let the other
             // stage's copy (if any) land, and leave
             if (tid == 0) {
-                atomicOr((unsigned long long *)&inst[info[b].x].clock[2], 1ull);
+                atomicOr((unsigned long long *)&inst[inf.x].clock[2], 1ull);
                 if (tile + (int)gridDim.x < total_tiles) mbar_wait_bounded(&bar[b ^ 1], ((k + 1) >> 1) & 1);
             }
             return;
         }
-        const int nxt = tile + 2 * (int)gridDim.x;
-        if (tid == 0 && nxt < total_tiles) issue(nxt, b);
+        if (tid == 0) {
+            const int nxt = tile + 2 * (int)gridDim.x;
+            if (nxt < total_tiles) issue(nxt, b);
+        }
     }
 }
 
@@ -696,7 +648,7 @@ __global__ void energy_kernel(const InstDesc *__restrict__ dd) {
 
 // ---------------------------------------------------------------- launchers
 namespace {
-template <typename T> size_t stencil_smem() { return (size_t)3 * SY * SX * sizeof(T); }
+template <typename T> size_t stencil_smem() { return (size_t)3 * SY * BOX_X * sizeof(T); }
 
 template <typename T> cudaError_t setup_stencil_attr() {
     static bool done = false;
@@ -751,7 +703,7 @@ bool encode_tensor_maps(const InstDesc &d, void *host_out, std::string &err) {
     const cuuint64_t dims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, 3};
     const cuuint64_t strides[2] = {(cuuint64_t)d.pitch * 4, (cuuint64_t)d.plane * 4};
     const cuuint32_t estr[3] = {1, 1, 1};
-    const cuuint32_t halo_box[3] = {TB_X, TB_Y, 3};
+    const cuuint32_t halo_box[3] = {BOX_X, TB_Y, 3};
     const cuuint32_t tile_box[3] = {TILE_X, TMA_TILE_Y, 3};
     for (int b = 0; b < 4; ++b) {
         CUresult r = enc(&maps[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, d.q[b < 3 ? b : 0], dims, strides,
