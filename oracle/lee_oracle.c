@@ -22,7 +22,10 @@
  *   4th-order 5-point Lagrange stencils (rows 0,1) and the central 5-point
  *   stencil (row 2).  Radiation condition in the three outer layers:
  *   dq/dt = -(cos th dq/dx + sin th dq/dy + q/(2 rho)), polar about the domain
- *   centre, no source there.  Normal n points from the wall into the fluid;
+ *   centre, no source there.  An absorbing ramp over the 12 outer layers
+ *   (damping rate (0.04 c0/h) ((12 - d)/12)^2 at distance d from the edge,
+ *   i.e. 2% per step at the edge for CFL 0.5) removes a slowly growing
+ *   boundary mode of this closure.  Normal n points from the wall into the fluid;
  *   u_n (positive into the wall) = -u.n, so the Dirichlet datum for w = u.n is
  *   -u_n and the Neumann datum for dp/dn is +du_n/dt.  Critical damping uses
  *   the double-pole (Jordan) form of the same admittance.
@@ -644,6 +647,21 @@ void orc_deriv_1d(int n, const double *f, double h, int per, double *out)
     for (int i = 0; i < n; i++) out[i] = deriv1(f, 1, n, i, per, h);
 }
 
+/* Absorbing ramp near the non-periodic edges: damping rate at node (i, j),
+ * (SPONGE_K / h) ((W - d) / W)^2 for a distance d < W (in cells) to the
+ * nearest edge, 0 elsewhere. */
+#define SPONGE_W 12
+#define SPONGE_K 0.04
+static double sponge_rate(const orc_t *o, int i, int j)
+{
+    int d = 1 << 30;
+    if (!o->per_x) { if (i < d) d = i; if (o->nx - 1 - i < d) d = o->nx - 1 - i; }
+    if (!o->per_y) { if (j < d) d = j; if (o->ny - 1 - j < d) d = o->ny - 1 - j; }
+    if (d >= SPONGE_W) return 0.0;
+    double r = (double)(SPONGE_W - d) / SPONGE_W;
+    return SPONGE_K / o->h * r * r;
+}
+
 static int in_band(const orc_t *o, int i, int j)
 {
     return (!o->per_x && (i < 3 || i > o->nx - 4)) || (!o->per_y && (j < 3 || j > o->ny - 4));
@@ -724,6 +742,9 @@ static void orc_rhs(orc_t *o, double *q[3], const double *X, double sigma, doubl
                 rq[1][s] = -dx_at(o, q[0], i, j);
                 rq[2][s] = -dy_at(o, q[0], i, j);
             }
+            double sr = sponge_rate(o, i, j);
+            if (sr != 0.0)
+                for (int f = 0; f < 3; f++) rq[f][s] -= sr * q[f][s];
         }
 }
 

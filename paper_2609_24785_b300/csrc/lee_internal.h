@@ -25,6 +25,14 @@ constexpr int MAX_PROBES = 1024;
 // tile flags
 constexpr uint32_t TILE_BAND = 1u;      // output region meets the 3 outer layers
 constexpr uint32_t TILE_MIXED = 2u;     // has non-fluid or out-of-grid outputs
+constexpr uint32_t TILE_SPONGE = 4u;    // meets the absorbing ramp along the outer edges
+
+// Absorbing ramp along the non-periodic edges: damping rate
+// (SPONGE_K / h) ((SPONGE_W - d) / SPONGE_W)^2 at a distance d < SPONGE_W cells
+// from the nearest edge (2% per step at the edge for CFL 0.5).  It removes a
+// slowly growing mode of the one-sided/radiation closure on large domains.
+constexpr int SPONGE_W = 12;
+constexpr double SPONGE_K = 0.04;
 
 // Combined FP64 weight row entry of one cloud node: p_BP = sum l0 p,
 // Neumann row wp, Dirichlet row wd, free-extrapolation row wf.

@@ -90,16 +90,28 @@ ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int4 *__restric
     T *U = P + d.plane;
     T *V = P + 2 * d.plane;
     double s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0;
-    for (int e = e0 + lane; e < e1; e += GHOST_LANES) {
-        const int idx = __ldg(d.e_idx + e);
-        const GW w = ldg_gw(d.e_w + e);
-        const double p = (double)P[idx], u = (double)U[idx], v = (double)V[idx];
+    auto accumulate = [&](const GW &w, double p, double u, double v) {
         s0 = fma(w.l0, p, s0);       // L0 . p      -> p_BP          (step 1)
         s1 = fma(w.wp, p, s1);       // w_p . p     (Neumann row)
         s2 = fma(w.wd, u, s2);       // w_d . u     (Dirichlet row)
         s3 = fma(w.wd, v, s3);
         s4 = fma(w.wf, u, s4);       // w_f . u     (free row)
         s5 = fma(w.wf, v, s5);
+    };
+    // two entries per lane per round: all loads of both are issued first
+    int e = e0 + lane;
+    for (; e + GHOST_LANES < e1; e += 2 * GHOST_LANES) {
+        const int ia = __ldg(d.e_idx + e), ib = __ldg(d.e_idx + e + GHOST_LANES);
+        const GW wa = ldg_gw(d.e_w + e), wb = ldg_gw(d.e_w + e + GHOST_LANES);
+        const double pa = (double)P[ia], ua = (double)U[ia], va = (double)V[ia];
+        const double pb = (double)P[ib], ub = (double)U[ib], vb = (double)V[ib];
+        accumulate(wa, pa, ua, va);
+        accumulate(wb, pb, ub, vb);
+    }
+    if (e < e1) {
+        const int ia = __ldg(d.e_idx + e);
+        const GW wa = ldg_gw(d.e_w + e);
+        accumulate(wa, (double)P[ia], (double)U[ia], (double)V[ia]);
     }
     const unsigned gmask = 0xffu << (threadIdx.x & 24);
 #pragma unroll
@@ -138,7 +150,7 @@ ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int4 *__restric
 // Shared-memory halo box: the tile's outputs plus HALO nodes on every side.
 constexpr int BOX_X = TILE_X + 2 * HALO;                    // 72
 constexpr int THREADS_X = TILE_X / 4;                       // 16 threads across, 4 columns each
-constexpr int RY = 4;                                       // rows per thread
+constexpr int RY = 4;                                       // rows per thread (shared-memory kernel)
 constexpr int LIST_CAP = 1024;                              // band points per tile (<= 3 (64 + 64))
 
 template <typename T> struct alignas(4 * sizeof(T)) Vec4 { T v[4]; };
@@ -165,6 +177,17 @@ __device__ __forceinline__ T deriv_general(F f, int x, int n, int per, T inv_h) 
     return (f(-2) - T(8) * f(-1) + T(8) * f(1) - f(2)) * i12;              // x == n - 3
 }
 
+// ((W - d) / W)^2 of the absorbing ramp at node (gx, gy), 0 outside it
+template <typename T>
+__device__ __forceinline__ T ramp2(const InstDesc &d, int gx, int gy) {
+    int dist = 1 << 30;
+    if (!d.per_x) dist = min(dist, min(gx, d.nx - 1 - gx));
+    if (!d.per_y) dist = min(dist, min(gy, d.ny - 1 - gy));
+    if (dist >= SPONGE_W) return T(0);
+    const T r = (T)(SPONGE_W - dist) / (T)SPONGE_W;
+    return r * r;
+}
+
 __device__ __forceinline__ double stage_sigma(const InstDesc &d, int stage) {
     const double tn = (double)d.clock[0] * d.dt;
     double sn, cs;
@@ -186,7 +209,7 @@ template <typename T> struct QnSrc {
 // are appended to `list` and done afterwards by band_points().
 //   FOLD: FP32 form q - sum_j k_j (f_{+j} - f_{-j}), k_j = alpha dt a_j / h;
 //   else: q + alpha dt RHS with RHS from the DRP derivatives times 1/h.
-template <typename T, bool FOLD>
+template <typename T, bool FOLD, int RY>
 __device__ __forceinline__ void tile_points(const T *sp, const T *su, const T *sv, const QnSrc<T> &qn,
                                             const InstDesc &d, T *out, int xt, int yt, uint32_t flags, int stage,
                                             T src, int txi, int tyi, unsigned short *list, int *list_n) {
@@ -199,12 +222,14 @@ __device__ __forceinline__ void tile_points(const T *sp, const T *su, const T *s
     const T inv_h = (T)d.inv_h;
     const double adh = c_alpha[stage - 1] * d.dt * d.inv_h;
     const T k1 = (T)(adh * 0.770882380518), k2 = (T)(adh * -0.166705904415), k3 = (T)(adh * 0.020843142770);
+    const T ksp = (T)(adh * SPONGE_K);            // alpha dt (SPONGE_K / h), folded form
+    const T sk_h = (T)(SPONGE_K * d.inv_h);       // SPONGE_K / h
     const T *gxs = (const T *)d.gx;
     const T *gys = (const T *)d.gy;
     if (gx0 >= nx || gy0 >= ny) return;
 
     // y differences of p and v on the thread's 4 columns
-    T dpy[RY][4], dvy[RY][4];
+    T dpy[RY][4], dvy[RY][4], vc[RY][4];
     {
         T cp[RY + 6][4], cv[RY + 6][4];
 #pragma unroll
@@ -218,6 +243,7 @@ __device__ __forceinline__ void tile_points(const T *sp, const T *su, const T *s
         for (int r = 0; r < RY; ++r)
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
+                vc[r][q] = cv[r + 3][q];
                 if (FOLD) {
                     dpy[r][q] = k1 * (cp[r + 4][q] - cp[r + 2][q]) + k2 * (cp[r + 5][q] - cp[r + 1][q]) +
                                 k3 * (cp[r + 6][q] - cp[r][q]);
@@ -266,22 +292,34 @@ __device__ __forceinline__ void tile_points(const T *sp, const T *su, const T *s
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int c = 4 + q;
+            // absorbing ramp: rate (SPONGE_K / h) ramp2
+            const T rr = (flags & TILE_SPONGE) ? ramp2<T>(d, gx0 + q, gy) : T(0);
             if (FOLD) {
                 const T dpx = k1 * (wp[c + 1] - wp[c - 1]) + k2 * (wp[c + 2] - wp[c - 2]) + k3 * (wp[c + 3] - wp[c - 3]);
                 const T dux = k1 * (wu[c + 1] - wu[c - 1]) + k2 * (wu[c + 2] - wu[c - 2]) + k3 * (wu[c + 3] - wu[c - 3]);
                 T op = n0.v[q] - (dux + dvy[r][q]);
                 if (src != T(0)) op += ad * sy * gxs[gx0 + q];
+                T ou = n1.v[q] - dpx, ov = n2.v[q] - dpy[r][q];
+                if (rr != T(0)) {
+                    const T ks = ksp * rr;
+                    op -= ks * wp[c]; ou -= ks * wu[c]; ov -= ks * vc[r][q];
+                }
                 o0.v[q] = op;
-                o1.v[q] = n1.v[q] - dpx;
-                o2.v[q] = n2.v[q] - dpy[r][q];
+                o1.v[q] = ou;
+                o2.v[q] = ov;
             } else {
                 const T dpdx = drp<T>(wp[c - 3], wp[c - 2], wp[c - 1], wp[c + 1], wp[c + 2], wp[c + 3]) * inv_h;
                 const T dudx = drp<T>(wu[c - 3], wu[c - 2], wu[c - 1], wu[c + 1], wu[c + 2], wu[c + 3]) * inv_h;
                 T rp = -(dudx + dvy[r][q]);
                 if (src != T(0)) rp += sy * gxs[gx0 + q];
+                T ru = -dpdx, rv = -dpy[r][q];
+                if (rr != T(0)) {
+                    const T sg = sk_h * rr;
+                    rp -= sg * wp[c]; ru -= sg * wu[c]; rv -= sg * vc[r][q];
+                }
                 o0.v[q] = n0.v[q] + ad * rp;
-                o1.v[q] = n1.v[q] + ad * (-dpdx);
-                o2.v[q] = n2.v[q] + ad * (-dpy[r][q]);
+                o1.v[q] = n1.v[q] + ad * ru;
+                o2.v[q] = n2.v[q] + ad * rv;
             }
         }
         const long long o = (long long)gy * pitch + gx0;
@@ -335,9 +373,10 @@ __device__ __forceinline__ void band_points(const T *sp, const T *su, const T *s
         const T rho = sqrt(rx * rx + ryy * ryy);
         const T ct = rx / rho, st = ryy / rho;
         const T q2 = half_inv_h / rho;                               // 1 / (2 h rho)
-        const T rp = -(ct * dpdx + st * dpdy + sp[sr * BOX_X + sc] * q2);
-        const T ru = -(ct * dudx + st * dudy + su[sr * BOX_X + sc] * q2);
-        const T rv = -(ct * dvdx + st * dvdy + sv[sr * BOX_X + sc] * q2);
+        const T sg = (T)(SPONGE_K * d.inv_h) * ramp2<T>(d, gx, gy);
+        const T rp = -(ct * dpdx + st * dpdy + sp[sr * BOX_X + sc] * q2) - sg * sp[sr * BOX_X + sc];
+        const T ru = -(ct * dudx + st * dudy + su[sr * BOX_X + sc] * q2) - sg * su[sr * BOX_X + sc];
+        const T rv = -(ct * dvdx + st * dvdy + sv[sr * BOX_X + sc] * q2) - sg * sv[sr * BOX_X + sc];
         const long long o = (long long)gy * d.pitch + gx;
         const long long oq = qn.at(lx, ly);
         out[o] = qn.p[oq] + ad * rp;
@@ -419,7 +458,7 @@ stencil_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__restri
             qn = QnSrc<T>{q0, q0 + plane, q0 + 2 * plane, pitch};
         }
         T *out = (T *)d.q[outb];
-        tile_points<T, false>(sp, su, sv, qn, d, out, xt, yt, flags, stage, s_src, txi, tyi, list, &list_n);
+        tile_points<T, false, RY>(sp, su, sv, qn, d, out, xt, yt, flags, stage, s_src, txi, tyi, list, &list_n);
         if (flags & TILE_BAND) {
             __syncthreads();
             band_points<T>(sp, su, sv, qn, d, out, xt, yt, stage, list, min(list_n, LIST_CAP), threadIdx.x,
@@ -437,7 +476,7 @@ stencil_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__restri
 // stage, the copies of tile i + 1 land in the other.  Completion is tracked by
 // one mbarrier per stage (expect_tx); every wait is bounded.
 constexpr int TB_Y = TMA_TILE_Y + 2 * HALO;                 // 72
-constexpr int TMA_THREADS = THREADS_X * (TMA_TILE_Y / RY);  // 256
+template <int RYT> __host__ __device__ constexpr int tma_threads() { return THREADS_X * (TMA_TILE_Y / RYT); }   // 256 or 512
 constexpr uint32_t HALO_BYTES = BOX_X * TB_Y * 3 * 4;       // 62208
 constexpr uint32_t QN_BYTES = TILE_X * TMA_TILE_Y * 3 * 4;  // 49152
 constexpr uint32_t STAGE_BYTES = HALO_BYTES + QN_BYTES;     // 111360 = 870 x 128
@@ -473,9 +512,11 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const void *map, uint64_t
         : "memory");
 }
 
-__global__ void __launch_bounds__(TMA_THREADS, 1)
+template <int RYT>
+__global__ void __launch_bounds__(tma_threads<RYT>(), 1)
 stencil_tma_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__restrict__ tprefix, int total_tiles,
                    int stage) {
+    constexpr int TMA_THREADS = tma_threads<RYT>();
     extern __shared__ unsigned char smem_dyn[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t bar[2];
@@ -538,8 +579,8 @@ stencil_tma_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__re
                 qn = QnSrc<float>{qp, qp + TILE_X * TMA_TILE_Y, qp + 2 * TILE_X * TMA_TILE_Y, TILE_X};
             }
             float *out = (float *)d.q[outb];
-            tile_points<float, true>(sp, su, sv, qn, d, out, inf.y, inf.z, (uint32_t)inf.w, stage, ssrc[b], txi,
-                                     tyi, list, &list_n[b]);
+            tile_points<float, true, RYT>(sp, su, sv, qn, d, out, inf.y, inf.z, (uint32_t)inf.w, stage, ssrc[b],
+                                          txi, tyi, list, &list_n[b]);
             if (inf.w & TILE_BAND) {
                 __syncthreads();
                 band_points<float>(sp, su, sv, qn, d, out, inf.y, inf.z, stage, list, min(list_n[b], LIST_CAP), tid,
@@ -671,12 +712,25 @@ int num_sms() {
     return n;
 }
 
+// rows per thread of the TMA kernel (4: 256 threads, 2: 512 threads)
+int tma_rows() {
+    static int r = [] {
+        const char *e = getenv("LEE_TMA_RY");
+        const int v = e ? atoi(e) : 2;
+        return v == 4 ? 4 : 2;
+    }();
+    return r;
+}
+
 cudaError_t prepare_kernels(int precision) {
     if (precision == 1) {
         static bool done = false;
         if (!done) {
-            cudaError_t e = cudaFuncSetAttribute(stencil_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaError_t e = cudaFuncSetAttribute(stencil_tma_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)TMA_SMEM);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(stencil_tma_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)TMA_SMEM);
             if (e != cudaSuccess) return e;
             done = true;
         }
@@ -706,9 +760,19 @@ bool encode_tensor_maps(const InstDesc &d, void *host_out, std::string &err) {
     const cuuint32_t halo_box[3] = {BOX_X, TB_Y, 3};
     const cuuint32_t tile_box[3] = {TILE_X, TMA_TILE_Y, 3};
     for (int b = 0; b < 4; ++b) {
+        // The halo box rows start 16 bytes before a 256-byte boundary: a 256-byte
+        // L2 promotion fetches ~2.7x the row from DRAM, so promotion is off
+        // unless LEE_TMA_PROMO asks for it (1: 64 B, 2: 128 B, 3: 256 B).
+        static const CUtensorMapL2promotion promo = [] {
+            const char *e = getenv("LEE_TMA_PROMO");
+            const int v = e ? atoi(e) : 0;
+            return v == 1 ? CU_TENSOR_MAP_L2_PROMOTION_L2_64B
+                 : v == 2 ? CU_TENSOR_MAP_L2_PROMOTION_L2_128B
+                 : v == 3 ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B : CU_TENSOR_MAP_L2_PROMOTION_NONE;
+        }();
         CUresult r = enc(&maps[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, d.q[b < 3 ? b : 0], dims, strides,
                          b < 3 ? halo_box : tile_box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                         promo, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
             err = "cuTensorMapEncodeTiled returned " + std::to_string((int)r);
             return false;
@@ -732,7 +796,12 @@ cudaError_t launch_stencil(const BatchView &bv, int stage, int persistent_ctas, 
     if (bv.precision == 1 && bv.use_tma) {
         if (bv.total_tiles == 0) return cudaSuccess;
         const int grid = std::min(bv.total_tiles, persistent_ctas > 0 ? persistent_ctas : num_sms());
-        stencil_tma_kernel<<<grid, TMA_THREADS, TMA_SMEM, s>>>(bv.inst, bv.ninst, bv.tile_prefix, bv.total_tiles, stage);
+        if (tma_rows() == 4)
+            stencil_tma_kernel<4><<<grid, tma_threads<4>(), TMA_SMEM, s>>>(bv.inst, bv.ninst, bv.tile_prefix,
+                                                                          bv.total_tiles, stage);
+        else
+            stencil_tma_kernel<2><<<grid, tma_threads<2>(), TMA_SMEM, s>>>(bv.inst, bv.ninst, bv.tile_prefix,
+                                                                          bv.total_tiles, stage);
         count_launch();
         return cudaGetLastError();
     }

@@ -413,6 +413,8 @@ int build_plan(int nx, int ny, double h, double x0, double y0, int per_x, int pe
             if (!per_x && (xa < 3 || xb > nx - 3)) f |= TILE_BAND;
             if (!per_y && (ya < 3 || yb > ny - 3)) f |= TILE_BAND;
             if (per_x || per_y) f |= TILE_BAND;        // wrapped halos take the general path
+            if ((!per_x && (xa < SPONGE_W || xb > nx - SPONGE_W)) || (!per_y && (ya < SPONGE_W || yb > ny - SPONGE_W)))
+                f |= TILE_SPONGE;
             if (xb > nx || yb > ny) f |= TILE_MIXED;
             for (int j = ya; j < std::min(yb, ny) && !(f & TILE_MIXED); ++j)
                 for (int i = xa; i < std::min(xb, nx); ++i)

