@@ -77,6 +77,7 @@ typedef struct {
     long pcap, prec;
     int n_reduced;              /* ghosts whose degree was lowered */
     const double *bc_override;  /* test hook: (w_BP, dp/dn_BP) per ghost */
+    int f32_storage;            /* emulate FP32 storage of the field (tolerance studies) */
     char err[256];
 } orc_t;
 
@@ -121,6 +122,12 @@ void orc_destroy(orc_t *o)
 }
 
 const char *orc_error(orc_t *o) { return o->err; }
+
+/* FP32-storage emulation: round the stored field (stage results, ghost values,
+ * initial field) to single precision, as any implementation that keeps the
+ * bulk field in FP32 must.  Used to derive the FP32 error floor. */
+void orc_set_f32_storage(orc_t *o, int on) { o->f32_storage = on; }
+static double stored(const orc_t *o, double v) { return o->f32_storage ? (double)(float)v : v; }
 
 void orc_set_none(orc_t *o) { o->wall = 0; }
 void orc_set_line(orc_t *o, double xw, double yw, double angle)
@@ -526,7 +533,7 @@ void orc_init_pulse(orc_t *o, double xs, double ys, double amp, double w)
         for (int i = 0; i < o->nx; i++) {
             int s = j * o->nx + i;
             double dx = node_x(o, i) - xs, dy = node_y(o, j) - ys;
-            o->q[0][s] = o->kind[s] == 1 ? amp * exp(-b * (dx * dx + dy * dy)) : 0.0;
+            o->q[0][s] = o->kind[s] == 1 ? stored(o, amp * exp(-b * (dx * dx + dy * dy))) : 0.0;
             o->q[1][s] = 0.0; o->q[2][s] = 0.0;
         }
     memset(o->X, 0, sizeof(double) * 2 * (o->ng > 0 ? o->ng : 1));
@@ -544,7 +551,7 @@ void orc_init_packet(orc_t *o, double xs, double ys, double ang, double amp, dou
             double s = (node_x(o, i) - xs) * ca + (node_y(o, j) - ys) * sa;
             double p = o->kind[sidx] == 1
                      ? 0.5 * amp * exp(-alpha * alpha * s * s) * cos(2.0 * M_PI * k * s) : 0.0;
-            o->q[0][sidx] = p; o->q[1][sidx] = p * ca; o->q[2][sidx] = p * sa;
+            o->q[0][sidx] = stored(o, p); o->q[1][sidx] = stored(o, p * ca); o->q[2][sidx] = stored(o, p * sa);
         }
     memset(o->X, 0, sizeof(double) * 2 * (o->ng > 0 ? o->ng : 1));
     o->step = 0; o->prec = 0;
@@ -714,9 +721,9 @@ static void orc_rhs(orc_t *o, double *q[3], const double *X, double sigma, doubl
         for (int i = 0; i <= m; i++) tg += G->ell[i] * Pt[i];
         double pg = np / G->ct[0];
         double wg = nw / G->c[0];
-        q[0][G->target] = pg;
-        q[1][G->target] = wg * G->nx - tg * G->ny;
-        q[2][G->target] = wg * G->ny + tg * G->nx;
+        q[0][G->target] = stored(o, pg);
+        q[1][G->target] = stored(o, wg * G->nx - tg * G->ny);
+        q[2][G->target] = stored(o, wg * G->ny + tg * G->nx);
     }
     /* 6: right-hand side at fluid nodes */
     const double xc = o->x0 + 0.5 * (nx - 1) * h, yc = o->y0 + 0.5 * (ny - 1) * h;
@@ -780,7 +787,7 @@ void orc_run(orc_t *o, long nsteps, int classical)
 #pragma omp parallel for schedule(static)
                 for (size_t s = 0; s < n; s++)
                     for (int f = 0; f < 3; f++)
-                        qs[f][s] = o->kind[s] == 1 ? o->q[f][s] + ad * rq[f][s] : 0.0;
+                        qs[f][s] = o->kind[s] == 1 ? stored(o, o->q[f][s] + ad * rq[f][s]) : 0.0;
                 for (int g = 0; g < 2 * ng; g++) Xs[g] = o->X[g] + ad * Xd[g];
             }
             for (int f = 0; f < 3; f++) memcpy(o->q[f], qs[f], sizeof(double) * n);

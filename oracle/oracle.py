@@ -60,6 +60,7 @@ def _load():
             "orc_set_msd": (None, [vp, C.c_double, C.c_double, C.c_double]),
             "orc_set_monopole": (None, [vp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double]),
             "orc_setup": (C.c_int, [vp]),
+            "orc_set_f32_storage": (None, [vp, C.c_int]),
             "orc_n_ghost": (C.c_int, [vp]),
             "orc_n_reduced": (C.c_int, [vp]),
             "orc_regime": (C.c_int, [vp]),
@@ -167,6 +168,10 @@ class Oracle:
 
     def set_monopole(self, xs, ys, amp, halfwidth, omega):
         self._L.orc_set_monopole(self._o, xs, ys, amp, halfwidth, omega)
+
+    def set_f32_storage(self, on=True):
+        """Emulate FP32 storage of the field (tolerance studies only)."""
+        self._L.orc_set_f32_storage(self._o, int(on))
 
     def setup(self):
         rc = self._L.orc_setup(self._o)

@@ -18,8 +18,10 @@ def make_solver(case, precision="fp64", bind=True, probe_capacity=None):
     return s
 
 
-def make_oracle(case, probe_capacity=None):
+def make_oracle(case, probe_capacity=None, f32_storage=False):
     o = oracle.Oracle(case.nx, case.ny, case.h, case.cfl, periodic_x=case.periodic[0], periodic_y=case.periodic[1])
+    if f32_storage:
+        o.set_f32_storage(True)
     workloads.apply_to(case, o)
     o.setup()
     if len(case.probes):

@@ -23,12 +23,14 @@ from _helpers import make_oracle, make_solver, field_error, rel_l2
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-12, "fp32": 1e-5}
-# The 128^2 flat wall is specified in FP64 only.  FP32 storage by itself (the
-# FP64 oracle with its state rounded to FP32 after every stage) leaves a
-# relative L2 of 4.6e-5 there after 400 steps, because the pulse leaves the
-# domain and the remaining field is ~30x smaller than the initial one; its
-# FP32 run is checked against twice that floor.
-FLAT_FP32_TOL = 1e-4
+# FP32 bars are max(1e-5, 3 x the FP32-storage floor): the floor is the same
+# error measure between the FP64 oracle and the oracle run with its stored
+# field rounded to FP32 after every stage (what any FP32-storage solver must
+# do); the factor 3 covers the FP32 arithmetic of the stencil, which rounds
+# about as often as the storage.  In the 1024^2 cylinder run the floor of the
+# ADE states reaches 1.0e-5 of their peak (step 2700), the field's stays at
+# 2.5e-6.
+FP32_FLOOR_FACTOR = 3.0
 
 
 def _norm3(o, fluid):
@@ -38,13 +40,13 @@ def _norm3(o, fluid):
 _ORACLE_RUNS = {}
 
 
-def run_oracle(case, steps, samples=10):
+def run_oracle(case, steps, samples=10, f32_storage=False):
     """Oracle run; returns it with the largest field and ADE-state norms seen
     (cached per case and step count: the FP64 and FP32 runs share it)."""
-    key = (case.name, repr(case.wall), repr(case.imp), repr(case.init), repr(case.source), steps)
+    key = (case.name, repr(case.wall), repr(case.imp), repr(case.init), repr(case.source), steps, f32_storage)
     if key in _ORACLE_RUNS:
         return _ORACLE_RUNS[key]
-    o = make_oracle(case)
+    o = make_oracle(case, f32_storage=f32_storage)
     fluid = o.kind() == 1
     qmax, xmax = _norm3(o, fluid), 0.0
     done = 0
@@ -60,31 +62,42 @@ def run_oracle(case, steps, samples=10):
     return o, fluid, qmax, xmax
 
 
-def _check(case, precision, steps=None, ade=True, probes=True, tol=None):
+def _errors(a, o, fluid, qmax, xmax):
+    """(field, ADE, probes) errors of run a against oracle run o."""
+    diff = np.sqrt(sum(np.sum((a.field(f)[fluid] - o.field(f)[fluid]) ** 2) for f in range(3)))
+    ea = float(np.linalg.norm(a.ade() - o.ade()) / xmax) if o.n_ghost and xmax > 0 else 0.0
+    ep = rel_l2(a.probes(), o.probes()) if o.probes().size else 0.0
+    return float(diff / qmax), ea, ep
+
+
+def _check(case, precision, steps=None, ade=True, probes=True):
     steps = case.steps if steps is None else steps
-    tol = TOL[precision] if tol is None else tol
     s = make_solver(case, precision)
     s.step(steps)
     s.sync()
     o, fluid, qmax, xmax = run_oracle(case, steps)
     assert s.steps_done() == steps == o.step
-    diff = np.sqrt(sum(np.sum((s.field(f)[fluid] - o.field(f)[fluid]) ** 2) for f in range(3)))
-    err = float(diff / qmax)
-    print("%s %s: field %.3e (final-norm relative %.3e)" % (case.name, precision, err, field_error(s, o)))
-    assert err <= tol, (case.name, precision, err)
+    err, ea, ep = _errors(s, o, fluid, qmax, xmax)
+    tol = [TOL[precision]] * 3
+    if precision == "fp32":
+        f32, _, _, _ = run_oracle(case, steps, f32_storage=True)
+        floor = _errors(f32, o, fluid, qmax, xmax)
+        tol = [max(TOL["fp32"], FP32_FLOOR_FACTOR * fl) for fl in floor]
+        print("%s fp32 storage floor: field %.3e ade %.3e probes %.3e" % ((case.name,) + floor))
+    print("%s %s: field %.3e (final-norm relative %.3e) ade %.3e probes %.3e" %
+          (case.name, precision, err, field_error(s, o), ea, ep))
+    assert err <= tol[0], (case.name, precision, err, tol[0])
     if ade and o.n_ghost and case.imp[0] == "msd" and xmax > 0:
-        ea = float(np.linalg.norm(s.ade() - o.ade()) / xmax)
-        assert ea <= tol, ("ade", ea)
+        assert ea <= tol[1], ("ade", ea, tol[1])
     if probes and len(case.probes):
-        ep = rel_l2(s.probes(), o.probes())
-        assert ep <= tol, ("probes", ep)
+        assert ep <= tol[2], ("probes", ep, tol[2])
     return s, o, err
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_flat_wall_128_critical_ade(precision, cuda_device):
     """Inclined impedance wall, 128^2, R = 2 sqrt(KM) (double pole), 400 steps."""
-    _check(workloads.flat_wall(128), precision, tol=FLAT_FP32_TOL if precision == "fp32" else None)
+    _check(workloads.flat_wall(128), precision)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
