@@ -144,6 +144,7 @@ class Oracle:
         self.nx, self.ny, self.h = nx, ny, h
         self._o = self._L.orc_create(nx, ny, h, cfl, x0, y0, int(periodic_x), int(periodic_y))
         self.dt = self._L.orc_dt(self._o)
+        self._nprobe = 0
 
     def __del__(self):
         if getattr(self, "_o", None):
@@ -245,6 +246,8 @@ class Oracle:
 
     def probes(self):
         n = self._nprobe
+        if n == 0:
+            return np.zeros((0, 0))
         buf = np.empty(max(1, self.step) * max(n, 1))
         rec = self._L.orc_get_probes(self._o, _d(buf))
         return buf[:rec * n].reshape(rec, n)
