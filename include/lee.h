@@ -208,6 +208,31 @@ const char *lee_batch_last_error(const lee_batch *b);
  * write disjoint buffers, so repeated launches are idempotent. */
 int lee_batch_launch(lee_batch *b, int stage, int what);
 
+/* ---- energy without device allocation ----------------------------------- */
+/* Maximum grid rows accepted by lee_energy_noalloc (its static scratch). */
+#define LEE_NOALLOC_MAX_ROWS 16384
+/* Acoustic energy 1/2 h^2 sum (p^2 + u^2 + v^2) over the nodes whose kind is
+ * fluid (1), written to *out (one double in device memory), for callers that
+ * cannot allocate device memory: their fields live in memory owned by another
+ * runtime or pool that hands out pointers but allows no cudaMalloc (nor an
+ * allocating library call) on their side.  The paper has no counterpart; this
+ * is a library utility.
+ *   p, u, v  device arrays of ny rows of `pitch` elements (FP64 or FP32 per
+ *            `precision`), mask: ny x pitch bytes (node kinds), nx <= pitch.
+ *   stream   cudaStream_t (void*, NULL = legacy default stream); asynchronous.
+ * The entry point allocates nothing: its scratch is a static device array of
+ * LEE_NOALLOC_MAX_ROWS doubles (128 KiB), held by every GPU that loads the
+ * library until the process exits.  ny > LEE_NOALLOC_MAX_ROWS is rejected with
+ * LEE_ERR_ARG and a message (lee_last_error(NULL)).  The first call on a
+ * device looks up the scratch's device address (cudaGetSymbolAddress) with
+ * that device current, so make the first call on each device before any stream
+ * capture.  All calls share the scratch; each call rewrites every entry it
+ * reads, so nothing needs clearing, but calls that overlap on the GPU (two
+ * streams, two host threads) race on it.  The summation order is fixed: two
+ * calls on the same data give bitwise the same result. */
+int lee_energy_noalloc(const void *p, const void *u, const void *v, const unsigned char *mask, int nx, int ny,
+                       long long pitch, int precision, double h, double *out, void *stream);
+
 /* ---- library --------------------------------------------------------------- */
 /* Kernel launches enqueued by this process so far (all contexts and batches). */
 long long lee_launch_count(void);

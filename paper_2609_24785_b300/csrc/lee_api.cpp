@@ -41,6 +41,10 @@ void append_chunks(std::vector<int4> &out, int inst, int ng) {
 
 }  // namespace
 
+namespace lee {
+void set_global_error(const std::string &msg) { g_create_err = msg; }
+}  // namespace lee
+
 struct lee_ctx {
     lee_grid g{};
     Geometry geo;

@@ -144,5 +144,7 @@ cudaError_t launch_from_staging(const InstDesc *dinst, const InstDesc &h, int wh
 cudaError_t launch_energy(const InstDesc *dinst, const InstDesc &h, cudaStream_t s);
 long long launch_count();
 void count_launch(int n = 1);
+// message for lee_last_error(NULL) (entry points without a context)
+void set_global_error(const std::string &msg);
 
 }  // namespace lee

@@ -88,6 +88,8 @@ SIGNATURES = {
     "lee_batch_step": (C.c_int, [_vp, C.c_longlong]),
     "lee_batch_last_error": (C.c_char_p, [_vp]),
     "lee_batch_launch": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "lee_energy_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, C.c_int, C.c_longlong, C.c_int, C.c_double,
+                                      _vp, _vp]),
     "lee_launch_count": (C.c_longlong, []),
     "lee_version": (C.c_char_p, []),
 }
