@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lee", choices=["lee", "reference"])
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "cylinder"])
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "cylinder", "free"])
     ap.add_argument("--count", type=int, default=512)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
@@ -64,6 +64,15 @@ def workload_cases(args, rank, accept=None):
         desc = ("batched cylinder-pulse sweep: %d instances, n^2 with n in {256,384,512,768,1024}, "
                 "cylinder r = 0.1 n, R/M/K log-uniform, seed %d" % (args.count, 24785 + rank))
         return cases, rejected, desc
+    if args.workload == "free":
+        # diagnostic: no wall, so every tile away from the outer band is interior
+        cases = []
+        for i in range(args.count if args.count != 512 else 128):
+            c = workloads.cylinder_pulse(1024)
+            c.name = "free_%d" % i
+            c.wall, c.imp = ("none",), ("rigid",)
+            cases.append(c)
+        return cases, 0, "wall-free 1024^2 pulses, %d instances (diagnostic)" % len(cases)
     c = workloads.cylinder_pulse(1024)
     return [c], 0, "cylinder pulse 1024^2, r = 50 cells, R=2 M=0.02 K=1"
 
@@ -198,7 +207,7 @@ def run_lee(args):
     def plan(case):
         s = lee.Solver(case.nx, case.ny, case.h, case.cfl, precision=args.precision)
         workloads.apply_to(case, s)
-        if len(case.probes):
+        if len(case.probes) and case.wall[0] != "none":
             s.set_probes(case.probes, 4096)
         s.plan()
         return s

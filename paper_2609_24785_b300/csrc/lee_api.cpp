@@ -26,8 +26,24 @@ constexpr int GRAPH_STEPS = 8;
 
 struct Layout {
     size_t q, mask, tiles, gt, gs, gn, gk, ei, ew, xn, xs, gx, gy, pi, pw, ph, clock, scratch, staging, desc,
-        prefix, chunks, tmap, total;
+        prefix, chunks, strips, tmap, total;
 };
+
+// TMA stencil work list of one instance: columns of tiles (instance, tile
+// column, first tile row, tiles), cut into segments of at most `seg` tiles so
+// that small batches still give every SM work
+void append_strips(std::vector<int4> &out, int inst, const InstDesc &d, int seg) {
+    for (int tx = 0; tx < d.tiles_x; ++tx)
+        for (int ty = 0; ty < d.tiles_y; ty += seg)
+            out.push_back(make_int4(inst, tx, ty, std::min(seg, d.tiles_y - ty)));
+}
+int strip_segment(long long total_tiles) {
+    return (int)std::max<long long>(1, (total_tiles + 2LL * num_sms() - 1) / (2LL * num_sms()));
+}
+// longest strips first, dealt round-robin to the persistent CTAs
+void sort_strips(std::vector<int4> &s) {
+    std::stable_sort(s.begin(), s.end(), [](const int4 &a, const int4 &b) { return a.w > b.w; });
+}
 
 inline int n_chunks(int ng) { return (ng + GHOSTS_PER_CTA - 1) / GHOSTS_PER_CTA; }
 
@@ -54,6 +70,7 @@ struct lee_ctx {
     int probe_cap = 0;
     bool planned = false, bound = false;
     Plan plan;
+    int kernel_mode = KERNEL_SMEM;
     Layout L{};
     char *dev = nullptr;
     cudaStream_t stream = nullptr;
@@ -61,6 +78,7 @@ struct lee_ctx {
     InstDesc *dd = nullptr;
     int *dprefix = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};   // [0]: 1 step, [1]: GRAPH_STEPS steps
+    int nstrips = 0;
     std::string err;
     size_t elem() const { return g.precision == LEE_FP32 ? 4 : 8; }
 };
@@ -126,6 +144,7 @@ Layout make_layout(const lee_ctx *c) {
     L.desc = take(sizeof(InstDesc));
     L.prefix = take(8 * 4);
     L.chunks = take((size_t)(n_chunks(ng) + 1) * sizeof(int4));
+    L.strips = take((size_t)(P.tiles_x * P.tiles_y + 1) * sizeof(int4));
     L.tmap = take(4 * 128);
     L.total = o;
     return L;
@@ -228,7 +247,11 @@ BatchView single_view(lee_ctx *c) {
     bv.tile_prefix = c->dprefix;
     bv.ghost_chunks = (const int4 *)(c->dev + c->L.chunks);
     bv.nchunks = n_chunks(c->hd.ng);
+    bv.strips = (const int4 *)(c->dev + c->L.strips);
+    bv.nstrips = c->nstrips;
     bv.use_tma = c->hd.use_tma;
+    bv.kernel_mode = c->hd.kernel_mode;
+    bv.tile_w = c->hd.tile_w;
     bv.probe_inst = c->dprefix + 4;
     bv.nprobe_inst = c->hd.np > 0 ? 1 : 0;
     bv.total_tiles = c->hd.ntiles;
@@ -327,9 +350,11 @@ int lee_plan(lee_ctx *ctx, lee_sizes *out) {
     const lee_grid &g = ctx->g;
     std::string err;
     const bool periodic = g.bc_x == LEE_BC_PERIODIC || g.bc_y == LEE_BC_PERIODIC;
-    const int tile_h = (g.precision == LEE_FP32 && !periodic) ? TMA_TILE_Y : TILE_Y;
+    ctx->kernel_mode = default_kernel_mode(g.precision, periodic);
+    int tile_w = TILE_X, tile_h = TILE_Y;
+    if (ctx->kernel_mode == KERNEL_TMA) tma_tile(tile_w, tile_h);
     int rc = build_plan(g.nx, g.ny, g.h, g.x0, g.y0, g.bc_x == LEE_BC_PERIODIC, g.bc_y == LEE_BC_PERIODIC,
-                        g.cfl * g.h, tile_h, ctx->geo, ctx->imp, ctx->probe_xy, ctx->plan, err);
+                        g.cfl * g.h, tile_w, tile_h, ctx->geo, ctx->imp, ctx->probe_xy, ctx->plan, err);
     if (rc != LEE_OK) return fail(ctx, rc, err);
     if (ctx->plan.ade_amp > 1.0) {
         char b[160];
@@ -406,6 +431,7 @@ int lee_bind(lee_ctx *ctx, void *dev_ptr, long long dev_bytes, void *stream) {
     d.nx = P.nx; d.ny = P.ny; d.pitch = P.pitch; d.tiles_x = P.tiles_x; d.tiles_y = P.tiles_y;
     d.ntiles = P.tiles_x * P.tiles_y;
     d.tile_h = P.tile_h;
+    d.tile_w = P.tile_w;
     d.per_x = ctx->g.bc_x == LEE_BC_PERIODIC; d.per_y = ctx->g.bc_y == LEE_BC_PERIODIC;
     d.h = ctx->g.h; d.inv_h = 1.0 / ctx->g.h; d.dt = ctx->g.cfl * ctx->g.h;
     d.cx = 0.5 * (P.nx - 1); d.cy = 0.5 * (P.ny - 1);
@@ -430,7 +456,15 @@ int lee_bind(lee_ctx *ctx, void *dev_ptr, long long dev_bytes, void *stream) {
     d.scratch = (double *)(ctx->dev + L.scratch);
     d.staging = (double *)(ctx->dev + L.staging);
     d.precision = ctx->g.precision;
-    d.use_tma = P.tile_h == TMA_TILE_Y;
+    d.kernel_mode = ctx->kernel_mode;
+    d.use_tma = ctx->kernel_mode == KERNEL_TMA;
+    {
+        std::vector<int4> strips;
+        append_strips(strips, 0, d, strip_segment((long long)d.tiles_x * d.tiles_y));
+        ctx->nstrips = (int)strips.size();
+        CK(cudaMemcpyAsync(ctx->dev + L.strips, strips.data(), strips.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+    }
     for (int q = 0; q < 4; ++q) d.tmap[q] = ctx->dev + L.tmap + 128 * q;
     if (d.use_tma) {
         alignas(64) unsigned char maps[4 * 128];
@@ -682,8 +716,9 @@ int lee_batch_add(lee_batch *b, lee_ctx *c) {
     if (!b || !c) return LEE_ERR_ARG;
     if (!c->bound) { b->err = "context not bound"; return LEE_ERR_ARG; }
     if (c->g.precision != b->precision) { b->err = "precision differs from the batch"; return LEE_ERR_ARG; }
-    if (!b->members.empty() && b->members[0]->hd.use_tma != c->hd.use_tma) {
-        b->err = "periodic and non-periodic FP32 instances use different stencil kernels: batch them separately";
+    if (!b->members.empty() && (b->members[0]->hd.kernel_mode != c->hd.kernel_mode ||
+                                b->members[0]->hd.tile_w != c->hd.tile_w)) {
+        b->err = "members use different stencil kernels (periodic axes or kernel selection): batch them separately";
         return LEE_ERR_ARG;
     }
     if (std::find(b->members.begin(), b->members.end(), c) != b->members.end()) { b->err = "already a member"; return LEE_ERR_ARG; }
@@ -703,9 +738,10 @@ int lee_batch_remove(lee_batch *b, lee_ctx *c) {
 
 static long long batch_bytes(const lee_batch *b) {
     const size_t n = std::max<size_t>(b->members.size(), 1);
-    size_t nch = 1;
-    for (auto *c : b->members) nch += n_chunks(c->hd.ng);
-    return (long long)(align_up(n * sizeof(InstDesc)) + 2 * align_up((n + 1) * 4) + align_up(nch * sizeof(int4)));
+    size_t nch = 1, nst = 1;
+    for (auto *c : b->members) { nch += n_chunks(c->hd.ng); nst += (size_t)c->hd.tiles_x * c->hd.tiles_y; }
+    return (long long)(align_up(n * sizeof(InstDesc)) + 2 * align_up((n + 1) * 4) + align_up(nch * sizeof(int4)) +
+                       align_up(nst * sizeof(int4)));
 }
 
 int lee_batch_plan(lee_batch *b, long long *device_bytes) {
@@ -728,25 +764,33 @@ static int batch_refresh(lee_batch *b) {
     if (batch_bytes(b) > b->bytes) { b->err = "batch buffer too small"; return LEE_ERR_BUDGET; }
     std::vector<InstDesc> descs(n);
     std::vector<int> tp(n + 1, 0), pi;
-    std::vector<int4> chunks;
+    std::vector<int4> chunks, strips;
     int total_ghosts = 0;
+    long long total_tiles = 0;
+    for (auto *c : b->members) total_tiles += c->hd.ntiles;
+    const int seg = strip_segment(total_tiles);
     for (size_t i = 0; i < n; ++i) {
         descs[i] = b->members[i]->hd;
         tp[i + 1] = tp[i] + descs[i].ntiles;
         append_chunks(chunks, (int)i, descs[i].ng);
+        append_strips(strips, (int)i, descs[i], seg);
         total_ghosts += descs[i].ng;
         if (descs[i].np > 0) pi.push_back((int)i);
     }
     pi.resize(std::max<size_t>(pi.size(), 1));
     chunks.resize(std::max<size_t>(chunks.size(), 1));
+    sort_strips(strips);
+    const int nstrips = (int)strips.size();
+    strips.resize(std::max<size_t>(strips.size(), 1));
     const size_t o_desc = 0, o_tp = align_up(n * sizeof(InstDesc)), o_pi = o_tp + align_up((n + 1) * 4),
-                 o_ch = o_pi + align_up((n + 1) * 4);
+                 o_ch = o_pi + align_up((n + 1) * 4), o_st = o_ch + align_up(chunks.size() * sizeof(int4));
     cudaError_t e;
     if (n) {
         if ((e = cudaMemcpyAsync(b->dev + o_desc, descs.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice, b->stream)) ||
             (e = cudaMemcpyAsync(b->dev + o_tp, tp.data(), (n + 1) * 4, cudaMemcpyHostToDevice, b->stream)) ||
             (e = cudaMemcpyAsync(b->dev + o_pi, pi.data(), pi.size() * 4, cudaMemcpyHostToDevice, b->stream)) ||
             (e = cudaMemcpyAsync(b->dev + o_ch, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream)) ||
+            (e = cudaMemcpyAsync(b->dev + o_st, strips.data(), strips.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream)) ||
             (e = cudaStreamSynchronize(b->stream))) {
             b->err = std::string("batch upload: ") + cudaGetErrorString(e);
             return LEE_ERR_CUDA;
@@ -758,7 +802,11 @@ static int batch_refresh(lee_batch *b) {
     bv.tile_prefix = (const int *)(b->dev + o_tp);
     bv.ghost_chunks = (const int4 *)(b->dev + o_ch);
     bv.nchunks = total_ghosts > 0 ? (int)chunks.size() : 0;
+    bv.strips = (const int4 *)(b->dev + o_st);
+    bv.nstrips = nstrips;
     bv.use_tma = n ? descs[0].use_tma : 0;
+    bv.kernel_mode = n ? descs[0].kernel_mode : KERNEL_SMEM;
+    bv.tile_w = n ? descs[0].tile_w : TILE_X;
     bv.probe_inst = (const int *)(b->dev + o_pi);
     bv.nprobe_inst = 0;
     for (auto *c : b->members) bv.nprobe_inst += c->hd.np > 0;

@@ -16,6 +16,10 @@ constexpr int TILE_X = 64;
 constexpr int TILE_Y = 32;
 constexpr int TMA_TILE_Y = 64;
 constexpr int GHOST_LANES = 8;          // lanes per ghost point in the ghost kernel
+// stencil kernel variants
+constexpr int KERNEL_SMEM = 0;          // threads stage the halo box in shared memory (64 x 32 tiles)
+constexpr int KERNEL_DIRECT = 1;        // interior tiles read global memory directly (64 x 32 tiles)
+constexpr int KERNEL_TMA = 2;           // FP32 TMA pipeline (64 x 64 tiles)
 constexpr int GHOST_THREADS = 256;
 constexpr int GHOSTS_PER_CTA = GHOST_THREADS / GHOST_LANES;
 constexpr int HALO = 4;                 // smem halo on each side (7-pt DRP needs 3,
@@ -44,9 +48,10 @@ struct InstDesc {
     long long plane;            // elements per plane = ny * pitch
     const uint8_t *mask;        // node kind, ny x pitch (0 solid, 1 fluid, 2 ghost)
     const uint32_t *tile_flags; // tiles_x * tiles_y
-    int nx, ny, pitch, tiles_x, tiles_y, ntiles, tile_h;
+    int nx, ny, pitch, tiles_x, tiles_y, ntiles, tile_w, tile_h;
     int per_x, per_y;
-    int use_tma;                // FP32 TMA stencil path
+    int use_tma;                // FP32 TMA stencil path (kernel_mode == KERNEL_TMA)
+    int kernel_mode;            // KERNEL_SMEM / KERNEL_DIRECT / KERNEL_TMA
     const void *tmap[4];        // CUtensorMap (device): halo boxes of Q^n, Q^a, Q^b; 64x64 box of Q^n
     double h, inv_h, dt;
     double cx, cy;              // domain centre in index units ((n-1)/2)
@@ -79,7 +84,7 @@ struct InstDesc {
 // Host-side plan of one instance.
 struct Plan {
     int nx = 0, ny = 0, pitch = 0;
-    int tiles_x = 0, tiles_y = 0, tile_h = TILE_Y;
+    int tiles_x = 0, tiles_y = 0, tile_w = TILE_X, tile_h = TILE_Y;
     std::vector<uint8_t> kind;          // ny * nx (host order, no pitch)
     std::vector<uint32_t> tile_flags;
     // ghosts
@@ -112,7 +117,7 @@ struct Impedance {
 };
 
 // host set-up (lee_setup.cpp); returns LEE_* status, message in err
-int build_plan(int nx, int ny, double h, double x0, double y0, int per_x, int per_y, double dt, int tile_h,
+int build_plan(int nx, int ny, double h, double x0, double y0, int per_x, int per_y, double dt, int tile_w, int tile_h,
                const Geometry &geo, const Impedance &imp, const std::vector<double> &probe_xy,
                Plan &plan, std::string &err);
 void stage_forcing_factors(double omega, double dt, double G_re[4], double G_im[4]);
@@ -124,7 +129,11 @@ struct BatchView {
     const int *tile_prefix;     // ninst + 1 (device)
     const int4 *ghost_chunks;   // (instance, first ghost, count, 0), one per ghost CTA (device)
     int nchunks;
+    const int4 *strips;         // (instance, tile column, first tile row, tiles), longest first (device)
+    int nstrips;
     int use_tma;
+    int kernel_mode;
+    int tile_w;
     const int *probe_inst;      // instances with probes (device), nprobe_inst entries
     int nprobe_inst;
     int total_tiles;
@@ -133,6 +142,8 @@ struct BatchView {
 };
 cudaError_t prepare_kernels(int precision);   // one-time function attributes (outside capture)
 int num_sms();
+int default_kernel_mode(int precision, bool periodic);
+void tma_tile(int &tile_w, int &tile_h);
 // TMA descriptors of one FP32 instance (host encode; 4 x 128 bytes)
 bool encode_tensor_maps(const InstDesc &d, void *host_out /* 4 x 128 B */, std::string &err);
 cudaError_t launch_ghost(const BatchView &bv, int stage, cudaStream_t s);

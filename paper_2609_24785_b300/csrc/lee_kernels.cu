@@ -204,13 +204,15 @@ template <typename T> struct QnSrc {
 };
 
 // Step 6 of Sec. 3.2 on one tile: stage update of every output node owned by
-// this thread (4 columns x RY rows).  Interior fluid nodes take the vector
+// this thread (4 columns x RY rows).  sp, su, sv point at the box origin
+// (tile origin - HALO in x and y) of Q(k-1), bs elements per row: a shared-
+// memory halo box, or global memory for interior tiles.  Interior fluid nodes take the vector
 // DRP path; non-fluid nodes get zeros; fluid nodes of the three outer layers
 // are appended to `list` and done afterwards by band_points().
 //   FOLD: FP32 form q - sum_j k_j (f_{+j} - f_{-j}), k_j = alpha dt a_j / h;
 //   else: q + alpha dt RHS with RHS from the DRP derivatives times 1/h.
 template <typename T, bool FOLD, int RY>
-__device__ __forceinline__ void tile_points(const T *sp, const T *su, const T *sv, const QnSrc<T> &qn,
+__device__ __forceinline__ void tile_points(const T *sp, const T *su, const T *sv, long long bs, const QnSrc<T> &qn,
                                             const InstDesc &d, T *out, int xt, int yt, uint32_t flags, int stage,
                                             T src, int txi, int tyi, unsigned short *list, int *list_n) {
     const int cx0 = HALO + 4 * txi, ry0 = HALO + RY * tyi;     // box coordinates of the first output
@@ -228,14 +230,28 @@ __device__ __forceinline__ void tile_points(const T *sp, const T *su, const T *s
     const T *gys = (const T *)d.gy;
     if (gx0 >= nx || gy0 >= ny) return;
 
+    // FP32: this thread's Q^n rows are loaded first so that their latency
+    // overlaps the shared-memory work below (FP64 loads them row by row to
+    // keep its registers)
+    constexpr bool PRELOAD = sizeof(T) == 4;
+    Vec4<T> qn0[PRELOAD ? RY : 1], qn1[PRELOAD ? RY : 1], qn2[PRELOAD ? RY : 1];
+    if (PRELOAD) {
+#pragma unroll
+        for (int r = 0; r < RY; ++r)
+            if (gy0 + r < ny) {
+                qn0[r] = ld4(qn.p + qn.at(lx0, ly0 + r));
+                qn1[r] = ld4(qn.u + qn.at(lx0, ly0 + r));
+                qn2[r] = ld4(qn.v + qn.at(lx0, ly0 + r));
+            }
+    }
     // y differences of p and v on the thread's 4 columns
     T dpy[RY][4], dvy[RY][4], vc[RY][4];
     {
         T cp[RY + 6][4], cv[RY + 6][4];
 #pragma unroll
         for (int r = 0; r < RY + 6; ++r) {
-            const Vec4<T> a = ld4(sp + (ry0 - 3 + r) * BOX_X + cx0);
-            const Vec4<T> c = ld4(sv + (ry0 - 3 + r) * BOX_X + cx0);
+            const Vec4<T> a = ld4(sp + (ry0 - 3 + r) * bs + cx0);
+            const Vec4<T> c = ld4(sv + (ry0 - 3 + r) * bs + cx0);
 #pragma unroll
             for (int q = 0; q < 4; ++q) { cp[r][q] = a.v[q]; cv[r][q] = c.v[q]; }
         }
@@ -279,14 +295,19 @@ __device__ __forceinline__ void tile_points(const T *sp, const T *su, const T *s
         T wp[12], wu[12];
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-            const Vec4<T> a = ld4(sp + (ry0 + r) * BOX_X + cx0 - 4 + 4 * q);
-            const Vec4<T> c = ld4(su + (ry0 + r) * BOX_X + cx0 - 4 + 4 * q);
+            const Vec4<T> a = ld4(sp + (ry0 + r) * bs + cx0 - 4 + 4 * q);
+            const Vec4<T> c = ld4(su + (ry0 + r) * bs + cx0 - 4 + 4 * q);
 #pragma unroll
             for (int e = 0; e < 4; ++e) { wp[4 * q + e] = a.v[e]; wu[4 * q + e] = c.v[e]; }
         }
-        const Vec4<T> n0 = ld4(qn.p + qn.at(lx0, ly0 + r));
-        const Vec4<T> n1 = ld4(qn.u + qn.at(lx0, ly0 + r));
-        const Vec4<T> n2 = ld4(qn.v + qn.at(lx0, ly0 + r));
+        Vec4<T> n0, n1, n2;
+        if (PRELOAD) {
+            n0 = qn0[r]; n1 = qn1[r]; n2 = qn2[r];
+        } else {
+            n0 = ld4(qn.p + qn.at(lx0, ly0 + r));
+            n1 = ld4(qn.u + qn.at(lx0, ly0 + r));
+            n2 = ld4(qn.v + qn.at(lx0, ly0 + r));
+        }
         const T sy = src != T(0) ? src * gys[gy] : T(0);
         Vec4<T> o0, o1, o2;
 #pragma unroll
@@ -347,7 +368,7 @@ __device__ __forceinline__ void tile_points(const T *sp, const T *su, const T *s
 // stencils (rows 0..2) and the radiation condition
 // dq/dt = -(cos th dq/dx + sin th dq/dy + q / (2 rho)), polar about the centre.
 template <typename T>
-__device__ __forceinline__ void band_points(const T *sp, const T *su, const T *sv, const QnSrc<T> &qn,
+__device__ __forceinline__ void band_points(const T *sp, const T *su, const T *sv, int bs, const QnSrc<T> &qn,
                                             const InstDesc &d, T *out, int xt, int yt, int stage,
                                             const unsigned short *list, int n, int tid, int nthreads) {
     const T inv_h = (T)d.inv_h, half_inv_h = T(0.5) * inv_h;
@@ -357,12 +378,12 @@ __device__ __forceinline__ void band_points(const T *sp, const T *su, const T *s
         const int lx = list[i] & 0xff, ly = list[i] >> 8;
         const int gx = xt + lx, gy = yt + ly;
         const int sr = HALO + ly, sc = HALO + lx;
-        auto fxp = [&](int q) { return sp[sr * BOX_X + sc + q]; };
-        auto fxu = [&](int q) { return su[sr * BOX_X + sc + q]; };
-        auto fxv = [&](int q) { return sv[sr * BOX_X + sc + q]; };
-        auto fyp = [&](int q) { return sp[(sr + q) * BOX_X + sc]; };
-        auto fyu = [&](int q) { return su[(sr + q) * BOX_X + sc]; };
-        auto fyv = [&](int q) { return sv[(sr + q) * BOX_X + sc]; };
+        auto fxp = [&](int q) { return sp[sr * bs + sc + q]; };
+        auto fxu = [&](int q) { return su[sr * bs + sc + q]; };
+        auto fxv = [&](int q) { return sv[sr * bs + sc + q]; };
+        auto fyp = [&](int q) { return sp[(sr + q) * bs + sc]; };
+        auto fyu = [&](int q) { return su[(sr + q) * bs + sc]; };
+        auto fyv = [&](int q) { return sv[(sr + q) * bs + sc]; };
         const T dpdx = deriv_general<T>(fxp, gx, d.nx, d.per_x, inv_h);
         const T dpdy = deriv_general<T>(fyp, gy, d.ny, d.per_y, inv_h);
         const T dudx = deriv_general<T>(fxu, gx, d.nx, d.per_x, inv_h);
@@ -374,9 +395,9 @@ __device__ __forceinline__ void band_points(const T *sp, const T *su, const T *s
         const T ct = rx / rho, st = ryy / rho;
         const T q2 = half_inv_h / rho;                               // 1 / (2 h rho)
         const T sg = (T)(SPONGE_K * d.inv_h) * ramp2<T>(d, gx, gy);
-        const T rp = -(ct * dpdx + st * dpdy + sp[sr * BOX_X + sc] * q2) - sg * sp[sr * BOX_X + sc];
-        const T ru = -(ct * dudx + st * dudy + su[sr * BOX_X + sc] * q2) - sg * su[sr * BOX_X + sc];
-        const T rv = -(ct * dvdx + st * dvdy + sv[sr * BOX_X + sc] * q2) - sg * sv[sr * BOX_X + sc];
+        const T rp = -(ct * dpdx + st * dpdy + sp[sr * bs + sc] * q2) - sg * sp[sr * bs + sc];
+        const T ru = -(ct * dudx + st * dudy + su[sr * bs + sc] * q2) - sg * su[sr * bs + sc];
+        const T rv = -(ct * dvdx + st * dvdy + sv[sr * bs + sc] * q2) - sg * sv[sr * bs + sc];
         const long long o = (long long)gy * d.pitch + gx;
         const long long oq = qn.at(lx, ly);
         out[o] = qn.p[oq] + ad * rp;
@@ -390,7 +411,10 @@ __device__ __forceinline__ void band_points(const T *sp, const T *su, const T *s
 constexpr int SY = TILE_Y + 2 * HALO;                       // 40 box rows
 constexpr int STENCIL_THREADS = THREADS_X * (TILE_Y / RY);  // 128
 
-template <typename T>
+// DIRECT: interior tiles (all outputs fluid, no band, no ramp) read Q(k-1)
+// straight from global memory (neighbour reuse through L1/L2, no barrier);
+// the other tiles stage their halo box in shared memory.
+template <typename T, bool DIRECT>
 __global__ void __launch_bounds__(STENCIL_THREADS)
 stencil_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__restrict__ tprefix,
                int total_tiles, int stage) {
@@ -414,6 +438,16 @@ stencil_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__restri
         const T *qin = (const T *)d.q[inb];
         const long long plane = d.plane;
         const int pitch = d.pitch, nx = d.nx, ny = d.ny;
+        T *out = (T *)d.q[outb];
+        if (DIRECT && flags == 0) {
+            const T *g0 = qin + (long long)(yt - HALO) * pitch + (xt - HALO);
+            const T *q0 = (const T *)d.q[0] + (long long)yt * pitch + xt;
+            const QnSrc<T> qn{q0, q0 + plane, q0 + 2 * plane, pitch};
+            const T src = d.s_amp != 0.0 ? (T)(d.s_amp * stage_sigma(d, stage)) : T(0);
+            tile_points<T, false, RY>(g0, g0 + plane, g0 + 2 * plane, pitch, qn, d, out, xt, yt, flags, stage, src,
+                                      txi, tyi, list, &list_n);
+            continue;
+        }
 
         // ---- halo box of Q(k-1) into shared memory
         constexpr int C4 = BOX_X / 4;
@@ -457,11 +491,11 @@ stencil_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__restri
             const T *q0 = (const T *)d.q[0] + (long long)yt * pitch + xt;
             qn = QnSrc<T>{q0, q0 + plane, q0 + 2 * plane, pitch};
         }
-        T *out = (T *)d.q[outb];
-        tile_points<T, false, RY>(sp, su, sv, qn, d, out, xt, yt, flags, stage, s_src, txi, tyi, list, &list_n);
+        tile_points<T, false, RY>(sp, su, sv, BOX_X, qn, d, out, xt, yt, flags, stage, s_src, txi, tyi, list,
+                                  &list_n);
         if (flags & TILE_BAND) {
             __syncthreads();
-            band_points<T>(sp, su, sv, qn, d, out, xt, yt, stage, list, min(list_n, LIST_CAP), threadIdx.x,
+            band_points<T>(sp, su, sv, BOX_X, qn, d, out, xt, yt, stage, list, min(list_n, LIST_CAP), threadIdx.x,
                            STENCIL_THREADS);
         }
         __syncthreads();
@@ -469,18 +503,24 @@ stencil_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__restri
 }
 
 // ---------------------------------------------------------------- TMA stencil (FP32)
-// Persistent CTAs (one per SM) walk the tile list.  For every 64 x 64 output
-// tile one thread issues two TMA tensor copies into a shared-memory stage: the
-// 72 x 72 halo box of Q(k-1) (p, u, v planes) and, for stages 2-4, the 64 x 64
-// box of Q^n.  Two stages are in flight: while tile i is computed from one
-// stage, the copies of tile i + 1 land in the other.  Completion is tracked by
-// one mbarrier per stage (expect_tx); every wait is bounded.
-constexpr int TB_Y = TMA_TILE_Y + 2 * HALO;                 // 72
-template <int RYT> __host__ __device__ constexpr int tma_threads() { return THREADS_X * (TMA_TILE_Y / RYT); }   // 256 or 512
-constexpr uint32_t HALO_BYTES = BOX_X * TB_Y * 3 * 4;       // 62208
-constexpr uint32_t QN_BYTES = TILE_X * TMA_TILE_Y * 3 * 4;  // 49152
-constexpr uint32_t STAGE_BYTES = HALO_BYTES + QN_BYTES;     // 111360 = 870 x 128
-constexpr size_t TMA_SMEM = 2 * (size_t)STAGE_BYTES + 1024;
+// Persistent CTAs (one per SM) walk vertical strips of 64 x 64 output tiles,
+// top to bottom, so that the upper halo rows of a tile were fetched by the
+// same SM one tile earlier and are served from L2.  Strips are dealt
+// round-robin (longest first).  One thread issues a TMA tensor copy of the
+// 72 x 72 halo box of Q(k-1) (p, u, v planes) into one of three shared-memory
+// stages, two tiles ahead of the tile being computed; completion is tracked by
+// one mbarrier per stage (expect_tx), every wait is bounded.  Q^n is read by
+// the threads straight into registers (coalesced 16-byte loads).
+// TMA tile geometries: TW x TH outputs, halo box (TW + 8) x (TH + 8) x 3
+template <int TW, int TH> struct TmaGeom {
+    static constexpr int BW = TW + 2 * HALO, BH = TH + 2 * HALO;
+    static constexpr uint32_t BYTES = (uint32_t)BW * BH * 3 * 4;          // one stage
+    static constexpr int STAGES = 3;
+    static constexpr size_t SMEM = STAGES * (size_t)BYTES + 1024;
+    static_assert(BYTES % 128 == 0, "stage size must keep 128-byte alignment");
+    static_assert(BW <= 256 && BH <= 256, "TMA box dimensions are at most 256");
+};
+template <int TW, int TH, int RYT> __host__ __device__ constexpr int tma_threads() { return (TW / 4) * (TH / RYT); }
 constexpr int WAIT_SPINS = 1 << 20;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -512,94 +552,94 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const void *map, uint64_t
         : "memory");
 }
 
-template <int RYT>
-__global__ void __launch_bounds__(tma_threads<RYT>(), 1)
-stencil_tma_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__restrict__ tprefix, int total_tiles,
-                   int stage) {
-    constexpr int TMA_THREADS = tma_threads<RYT>();
+template <int TW, int TH, int RYT>
+__global__ void __launch_bounds__(tma_threads<TW, TH, RYT>(), 1)
+stencil_tma_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ strips, int nstrips, int stage) {
+    constexpr int NT = tma_threads<TW, TH, RYT>();
+    using G = TmaGeom<TW, TH>;
+    constexpr int TMA_STAGES = G::STAGES;
+    constexpr uint32_t HALO_BYTES = G::BYTES;
+    constexpr int BW = G::BW, BH = G::BH;
     extern __shared__ unsigned char smem_dyn[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t bar[2];
-    __shared__ int4 info[2];          // (instance, x0, y0, flags) of the tile in each stage
-    __shared__ float ssrc[2];         // source amplitude x stage forcing of that tile's instance
+    __shared__ __align__(8) uint64_t bar[TMA_STAGES];
+    __shared__ int4 info[TMA_STAGES];  // (instance, x0, y0, flags) of the tile in each stage
+    __shared__ float ssrc[TMA_STAGES]; // source amplitude x stage forcing of that tile's instance
     __shared__ unsigned short list[LIST_CAP];
-    __shared__ int list_n[2];         // band-list counters, by tile parity
+    __shared__ int list_n[2];          // band-list counters, by tile parity
+    __shared__ int s_ntiles;
     __shared__ int abort_flag;
     const int tid = threadIdx.x;
     const int inb = stage_in(stage), outb = stage_out(stage);
-    const uint32_t bytes = stage == 1 ? HALO_BYTES : STAGE_BYTES;
+    // producer cursor (thread 0): strip blockIdx.x + j * gridDim.x, tile row r
+    int pj = 0, pr = 0;
 
-    auto issue = [&](int tile, int b) {           // thread 0: resolve the tile, start its copies
-        const int ii = find_inst(tprefix, ninst, tile);
-        const InstDesc &d = inst[ii];
-        const int lt = tile - __ldg(tprefix + ii);
-        const int tx = lt % d.tiles_x, ty = lt / d.tiles_x;
-        const int x0 = tx * TILE_X, y0 = ty * TMA_TILE_Y;
-        info[b] = make_int4(ii, x0, y0, (int)__ldg(d.tile_flags + lt));
+    auto issue_next = [&](int b) {            // thread 0: next tile of this CTA into stage b
+        const int4 st = __ldg(strips + blockIdx.x + pj * gridDim.x);
+        const InstDesc &d = inst[st.x];
+        const int ty = st.z + pr;
+        const int x0 = st.y * TW, y0 = ty * TH;
+        info[b] = make_int4(st.x, x0, y0, (int)__ldg(d.tile_flags + ty * d.tiles_x + st.y));
         ssrc[b] = d.s_amp != 0.0 ? (float)(d.s_amp * stage_sigma(d, stage)) : 0.f;
-        unsigned char *dst = base + (size_t)b * STAGE_BYTES;
-        mbar_arrive_expect_tx(&bar[b], bytes);
-        tma_load_3d(dst, d.tmap[inb], &bar[b], x0 - HALO, y0 - HALO, 0);
-        if (stage != 1) tma_load_3d(dst + HALO_BYTES, d.tmap[3], &bar[b], x0, y0, 0);
+        mbar_arrive_expect_tx(&bar[b], HALO_BYTES);
+        tma_load_3d(base + (size_t)b * HALO_BYTES, d.tmap[inb], &bar[b], x0 - HALO, y0 - HALO, 0);
+        if (++pr == st.w) { pr = 0; ++pj; }
     };
 
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        int n = 0;
+        for (int s = blockIdx.x; s < nstrips; s += gridDim.x) n += __ldg(strips + s).w;
+        s_ntiles = n;
+        for (int b = 0; b < TMA_STAGES; ++b) mbar_init(&bar[b], 1);
         abort_flag = 0;
         list_n[0] = list_n[1] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int b = 0; b < TMA_STAGES - 1 && b < n; ++b) issue_next(b);
     }
     __syncthreads();
-    if (tid == 0) {
-        if ((int)blockIdx.x < total_tiles) issue(blockIdx.x, 0);
-        if ((int)(blockIdx.x + gridDim.x) < total_tiles) issue(blockIdx.x + gridDim.x, 1);
-    }
-
-    const int txi = tid % THREADS_X, tyi = tid / THREADS_X;
-    int k = 0;
-    for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x, ++k) {
-        const int b = k & 1;
-        const uint32_t parity = (k >> 1) & 1;
+    const int ntiles = s_ntiles;
+    const int txi = tid % (TW / 4), tyi = tid / (TW / 4);
+    for (int k = 0; k < ntiles; ++k) {
+        const int b = k % TMA_STAGES;
+        const uint32_t parity = (k / TMA_STAGES) & 1;
+        // the stage freed at the end of tile k - 1 receives tile k + 2
+        if (tid == 0 && k + TMA_STAGES - 1 < ntiles) issue_next((k + TMA_STAGES - 1) % TMA_STAGES);
         if (!mbar_wait_bounded(&bar[b], parity)) atomicExch(&abort_flag, 1);
         // all threads are inside iteration k here: the counter of tile k + 1
         // (last used by tile k - 1) can be cleared
-        if (tid == 0) list_n[b ^ 1] = 0;
+        if (tid == 0) list_n[(k & 1) ^ 1] = 0;
         const int4 inf = info[b];
         if (!abort_flag) {
             const InstDesc &d = inst[inf.x];
-            const float *sp = (const float *)(base + (size_t)b * STAGE_BYTES);
-            const float *su = sp + BOX_X * TB_Y;
-            const float *sv = su + BOX_X * TB_Y;
+            const float *sp = (const float *)(base + (size_t)b * HALO_BYTES);
+            const float *su = sp + BW * BH;
+            const float *sv = su + BW * BH;
             QnSrc<float> qn;
             if (stage == 1) {
-                qn = QnSrc<float>{sp + HALO * BOX_X + HALO, su + HALO * BOX_X + HALO, sv + HALO * BOX_X + HALO, BOX_X};
+                qn = QnSrc<float>{sp + HALO * BW + HALO, su + HALO * BW + HALO, sv + HALO * BW + HALO, BW};
             } else {
-                const float *qp = sv + BOX_X * TB_Y;
-                qn = QnSrc<float>{qp, qp + TILE_X * TMA_TILE_Y, qp + 2 * TILE_X * TMA_TILE_Y, TILE_X};
+                const float *q0 = (const float *)d.q[0] + (long long)inf.z * d.pitch + inf.y;
+                qn = QnSrc<float>{q0, q0 + d.plane, q0 + 2 * d.plane, d.pitch};
             }
             float *out = (float *)d.q[outb];
-            tile_points<float, true, RYT>(sp, su, sv, qn, d, out, inf.y, inf.z, (uint32_t)inf.w, stage, ssrc[b],
-                                          txi, tyi, list, &list_n[b]);
+            tile_points<float, true, RYT>(sp, su, sv, BW, qn, d, out, inf.y, inf.z, (uint32_t)inf.w, stage,
+                                          ssrc[b], txi, tyi, list, &list_n[k & 1]);
             if (inf.w & TILE_BAND) {
                 __syncthreads();
-                band_points<float>(sp, su, sv, qn, d, out, inf.y, inf.z, stage, list, min(list_n[b], LIST_CAP), tid,
-                                   TMA_THREADS);
+                band_points<float>(sp, su, sv, BW, qn, d, out, inf.y, inf.z, stage, list, min(list_n[k & 1], LIST_CAP),
+                                   tid, NT);
             }
         }
-        __syncthreads();                               // every thread is done with this stage
+        __syncthreads();                               // every thread is done with stage b
         if (abort_flag) {
-            // a copy did not complete in time: flag the instance, let the other
-            // stage's copy (if any) land, and leave
+            // a copy did not complete in time: flag the instance, let the copies
+            // still in flight land, and leave
             if (tid == 0) {
                 atomicOr((unsigned long long *)&inst[inf.x].clock[2], 1ull);
-                if (tile + (int)gridDim.x < total_tiles) mbar_wait_bounded(&bar[b ^ 1], ((k + 1) >> 1) & 1);
+                for (int q = 1; q < TMA_STAGES && k + q < ntiles; ++q)
+                    mbar_wait_bounded(&bar[(k + q) % TMA_STAGES], ((k + q) / TMA_STAGES) & 1);
             }
             return;
-        }
-        if (tid == 0) {
-            const int nxt = tile + 2 * (int)gridDim.x;
-            if (nxt < total_tiles) issue(nxt, b);
         }
     }
 }
@@ -694,8 +734,11 @@ template <typename T> size_t stencil_smem() { return (size_t)3 * SY * BOX_X * si
 template <typename T> cudaError_t setup_stencil_attr() {
     static bool done = false;
     if (done) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(stencil_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(stencil_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)stencil_smem<T>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(stencil_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)stencil_smem<T>());
     if (e == cudaSuccess) done = true;
     return e;
 }
@@ -712,6 +755,16 @@ int num_sms() {
     return n;
 }
 
+// stencil kernel of an instance: LEE_FP32_KERNEL / LEE_FP64_KERNEL = tma (FP32
+// only), smem or direct; periodic instances use the shared-memory kernels
+int default_kernel_mode(int precision, bool periodic) {
+    const char *e = getenv(precision == 1 ? "LEE_FP32_KERNEL" : "LEE_FP64_KERNEL");
+    const std::string v = e ? e : (precision == 1 ? "tma" : "smem");
+    if (v == "direct") return KERNEL_DIRECT;
+    if (v == "smem" || periodic || precision != 1) return KERNEL_SMEM;
+    return KERNEL_TMA;
+}
+
 // rows per thread of the TMA kernel (4: 256 threads, 2: 512 threads)
 int tma_rows() {
     static int r = [] {
@@ -722,15 +775,18 @@ int tma_rows() {
     return r;
 }
 
+template <int TW, int TH, int RYT> cudaError_t tma_attr() {
+    return cudaFuncSetAttribute(stencil_tma_kernel<TW, TH, RYT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)TmaGeom<TW, TH>::SMEM);
+}
+
 cudaError_t prepare_kernels(int precision) {
     if (precision == 1) {
         static bool done = false;
         if (!done) {
-            cudaError_t e = cudaFuncSetAttribute(stencil_tma_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)TMA_SMEM);
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(stencil_tma_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)TMA_SMEM);
+            cudaError_t e = tma_attr<64, 64, 2>();
+            if (e == cudaSuccess) e = tma_attr<64, 64, 4>();
+            if (e == cudaSuccess) e = tma_attr<128, 32, 2>();
             if (e != cudaSuccess) return e;
             done = true;
         }
@@ -739,6 +795,17 @@ cudaError_t prepare_kernels(int precision) {
     }
     num_sms();
     return setup_stencil_attr<double>();
+}
+
+// TMA tile width of FP32 instances: LEE_TMA_TILE = 64x64 (default) or 128x32
+void tma_tile(int &tw, int &th) {
+    static int w = 0, h = 0;
+    if (!w) {
+        const char *e = getenv("LEE_TMA_TILE");
+        const std::string v = e ? e : "64x64";
+        if (v == "128x32") { w = 128; h = 32; } else { w = 64; h = 64; }
+    }
+    tw = w; th = h;
 }
 
 bool encode_tensor_maps(const InstDesc &d, void *host_out, std::string &err) {
@@ -757,8 +824,8 @@ bool encode_tensor_maps(const InstDesc &d, void *host_out, std::string &err) {
     const cuuint64_t dims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, 3};
     const cuuint64_t strides[2] = {(cuuint64_t)d.pitch * 4, (cuuint64_t)d.plane * 4};
     const cuuint32_t estr[3] = {1, 1, 1};
-    const cuuint32_t halo_box[3] = {BOX_X, TB_Y, 3};
-    const cuuint32_t tile_box[3] = {TILE_X, TMA_TILE_Y, 3};
+    const cuuint32_t halo_box[3] = {(cuuint32_t)(d.tile_w + 2 * HALO), (cuuint32_t)(d.tile_h + 2 * HALO), 3};
+    const cuuint32_t tile_box[3] = {(cuuint32_t)d.tile_w, (cuuint32_t)d.tile_h, 3};   // unused by the kernel
     for (int b = 0; b < 4; ++b) {
         // The halo box rows start 16 bytes before a 256-byte boundary: a 256-byte
         // L2 promotion fetches ~2.7x the row from DRAM, so promotion is off
@@ -793,26 +860,39 @@ cudaError_t launch_ghost(const BatchView &bv, int stage, cudaStream_t s) {
 
 cudaError_t launch_stencil(const BatchView &bv, int stage, int persistent_ctas, cudaStream_t s) {
     cudaError_t e;
-    if (bv.precision == 1 && bv.use_tma) {
+    if (bv.precision == 1 && bv.kernel_mode == KERNEL_TMA) {
         if (bv.total_tiles == 0) return cudaSuccess;
-        const int grid = std::min(bv.total_tiles, persistent_ctas > 0 ? persistent_ctas : num_sms());
-        if (tma_rows() == 4)
-            stencil_tma_kernel<4><<<grid, tma_threads<4>(), TMA_SMEM, s>>>(bv.inst, bv.ninst, bv.tile_prefix,
-                                                                          bv.total_tiles, stage);
+        const int grid = std::min(bv.nstrips, persistent_ctas > 0 ? persistent_ctas : num_sms());
+        if (bv.tile_w == 128)
+            stencil_tma_kernel<128, 32, 2><<<grid, tma_threads<128, 32, 2>(), TmaGeom<128, 32>::SMEM, s>>>(
+                bv.inst, bv.strips, bv.nstrips, stage);
+        else if (tma_rows() == 4)
+            stencil_tma_kernel<64, 64, 4><<<grid, tma_threads<64, 64, 4>(), TmaGeom<64, 64>::SMEM, s>>>(
+                bv.inst, bv.strips, bv.nstrips, stage);
         else
-            stencil_tma_kernel<2><<<grid, tma_threads<2>(), TMA_SMEM, s>>>(bv.inst, bv.ninst, bv.tile_prefix,
-                                                                          bv.total_tiles, stage);
+            stencil_tma_kernel<64, 64, 2><<<grid, tma_threads<64, 64, 2>(), TmaGeom<64, 64>::SMEM, s>>>(
+                bv.inst, bv.strips, bv.nstrips, stage);
         count_launch();
         return cudaGetLastError();
     }
     const int grid = persistent_ctas > 0 ? std::min(persistent_ctas, bv.total_tiles) : bv.total_tiles;
+    if (bv.kernel_mode == KERNEL_DIRECT) {
+        if (bv.precision == 1)
+            stencil_kernel<float, true><<<grid, STENCIL_THREADS, stencil_smem<float>(), s>>>(
+                bv.inst, bv.ninst, bv.tile_prefix, bv.total_tiles, stage);
+        else
+            stencil_kernel<double, true><<<grid, STENCIL_THREADS, stencil_smem<double>(), s>>>(
+                bv.inst, bv.ninst, bv.tile_prefix, bv.total_tiles, stage);
+        count_launch();
+        return cudaGetLastError();
+    }
     if (bv.precision == 1) {
         if ((e = setup_stencil_attr<float>()) != cudaSuccess) return e;
-        stencil_kernel<float><<<grid, STENCIL_THREADS, stencil_smem<float>(), s>>>(bv.inst, bv.ninst, bv.tile_prefix,
+        stencil_kernel<float, false><<<grid, STENCIL_THREADS, stencil_smem<float>(), s>>>(bv.inst, bv.ninst, bv.tile_prefix,
                                                                                   bv.total_tiles, stage);
     } else {
         if ((e = setup_stencil_attr<double>()) != cudaSuccess) return e;
-        stencil_kernel<double><<<grid, STENCIL_THREADS, stencil_smem<double>(), s>>>(bv.inst, bv.ninst, bv.tile_prefix,
+        stencil_kernel<double, false><<<grid, STENCIL_THREADS, stencil_smem<double>(), s>>>(bv.inst, bv.ninst, bv.tile_prefix,
                                                                                     bv.total_tiles, stage);
     }
     count_launch();

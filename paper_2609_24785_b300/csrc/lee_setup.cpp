@@ -209,14 +209,15 @@ void stage_forcing_factors(double omega, double dt, double G_re[4], double G_im[
     }
 }
 
-int build_plan(int nx, int ny, double h, double x0, double y0, int per_x, int per_y, double dt, int tile_h,
+int build_plan(int nx, int ny, double h, double x0, double y0, int per_x, int per_y, double dt, int tile_w, int tile_h,
                const Geometry &geo, const Impedance &imp, const std::vector<double> &probe_xy,
                Plan &P, std::string &err) {
     Setup S{nx, ny, per_x, per_y, h, x0, y0, geo};
     P = Plan();
     P.nx = nx; P.ny = ny;
     P.pitch = (nx + 31) / 32 * 32;
-    P.tiles_x = (nx + TILE_X - 1) / TILE_X;
+    P.tile_w = tile_w;
+    P.tiles_x = (nx + tile_w - 1) / tile_w;
     P.tile_h = tile_h;
     P.tiles_y = (ny + tile_h - 1) / tile_h;
     const size_t n = (size_t)nx * ny;
@@ -409,7 +410,7 @@ int build_plan(int nx, int ny, double h, double x0, double y0, int per_x, int pe
     for (int ty = 0; ty < P.tiles_y; ++ty)
         for (int tx = 0; tx < P.tiles_x; ++tx) {
             uint32_t f = 0;
-            const int xa = tx * TILE_X, xb = xa + TILE_X, ya = ty * tile_h, yb = ya + tile_h;
+            const int xa = tx * tile_w, xb = xa + tile_w, ya = ty * tile_h, yb = ya + tile_h;
             if (!per_x && (xa < 3 || xb > nx - 3)) f |= TILE_BAND;
             if (!per_y && (ya < 3 || yb > ny - 3)) f |= TILE_BAND;
             if (per_x || per_y) f |= TILE_BAND;        // wrapped halos take the general path
