@@ -11,6 +11,13 @@ updates per second (fluid nodes x 4 stages x steps / time).  The device
 working set (~10 GB) is far larger than L2, so no flush is needed.
 
 --workload cylinder times the single 1024^2 cylinder-pulse solve instead.
+
+Serving (rank 0, unless --no-serve): the first --serve-duration seconds of a
+Poisson stream (--serve-rate requests/s, seed 24786) of mixed solves (flat wall
+at U[0, 60] deg or cylinder of radius U[0.05, 0.15] n; n in {256 ... 2048};
+R/M/K as in the sweep; 1000-10000 steps) through the continuous-batching
+server (FP32 bulk, 80 GB budget), then the same trace through the plain
+per-solve FP64 path; p50/p99 latency (arrival -> result) and throughput.
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload (the reference arm).
 
@@ -46,6 +53,11 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-duration", type=float, default=0.05,
+                    help="seconds of Poisson arrivals of the serving trace")
+    ap.add_argument("--serve-fp64", type=int, default=1, help="also serve the trace per solve in FP64")
     return ap.parse_args()
 
 
@@ -55,6 +67,21 @@ def peaks():
         d = json.load(open(p))
         return float(d["hbm_gbs"]), "measured"
     return 6400.0, "fallback"
+
+
+def stencil_kernel_name(precision):
+    """The stencil kernel the library picks for non-periodic instances (its
+    LEE_FP32_KERNEL / LEE_FP64_KERNEL / LEE_TMA_TILE / LEE_TMA_RY selection)."""
+    if precision == "fp32":
+        mode = os.environ.get("LEE_FP32_KERNEL", "tma")
+        if mode == "tma":
+            tile = os.environ.get("LEE_TMA_TILE", "64x64")
+            ry = 4 if os.environ.get("LEE_TMA_RY") == "4" and tile == "64x64" else 2
+            w, h = tile.split("x") if tile in ("64x32", "128x32") else ("64", "64")
+            return "stencil_tma_kernel<%s,%s,%d>" % (w, h, ry)
+        return "stencil_kernel<float,%s>" % ("true" if mode == "direct" else "false")
+    mode = os.environ.get("LEE_FP64_KERNEL", "smem")
+    return "stencil_kernel<double,%s>" % ("true" if mode == "direct" else "false")
 
 
 def workload_cases(args, rank, accept=None):
@@ -171,6 +198,37 @@ def run_reference(args):
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def run_serving(args):
+    """Serving trace through the continuous-batching server (FP32) and, for
+    comparison, through the per-solve FP64 path."""
+    from paper_2609_24785_b300 import lee, serve, workloads
+    rejected = [0]
+
+    def accept(case):
+        s = lee.Solver(case.nx, case.ny, case.h, case.cfl, precision="fp32")
+        workloads.apply_to(case, s)
+        try:
+            s.plan()
+            return True
+        except lee.LeeError:
+            rejected[0] += 1
+            return False
+    trace = workloads.serving_trace(rate=args.serve_rate, duration=args.serve_duration, accept=accept)
+    sizes = sorted({c.nx for _, c in trace})
+    out = {"trace": "Poisson %.0f/s for %.3f s (seed 24786): %d requests, n in %s, %d-%d steps, "
+                    "%d draws redrawn (set-up rejected: unstable ADE)" %
+                    (args.serve_rate, args.serve_duration, len(trace), sizes,
+                     min(c.steps for _, c in trace), max(c.steps for _, c in trace), rejected[0]),
+           "budget_bytes": 80 * 10**9}
+    rep = serve.Server(serve.LeeBackend("fp32"), budget_bytes=80 * 10**9).run(trace, realtime=True)
+    out["fp32_batched"] = rep.summary()
+    if args.serve_fp64:
+        rep64 = serve.Server(serve.LeeBackend("fp64", batching=False), max_slots=1,
+                             budget_bytes=80 * 10**9).run(trace, realtime=True)
+        out["fp64_per_solve"] = rep64.summary()
+    return out
 
 
 def run_lee(args):
@@ -324,6 +382,10 @@ def run_lee(args):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "what": "per step: state of every instance H2D from pinned host memory, one step, probe record D2H"}
 
+    serving = None
+    if rank == 0 and not args.no_serve:
+        serving = run_serving(args)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         small = min(cases, key=lambda c: c.points)
@@ -342,7 +404,7 @@ def run_lee(args):
                        "parallelism": "replicas" if ws > 1 else "single GPU", "setup_s": round(t_setup, 2)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "stencil_kernel<%s> stage 2" % ("float" if elem == 4 else "double"),
+                         "kernel": stencil_kernel_name(args.precision) + " stage 2",
                          "launch_ms": st_ms, "alg_bytes_per_launch": int(alg_bytes),
                          "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind},
             "ghost_kernel_ms": gh_ms,
@@ -350,6 +412,7 @@ def run_lee(args):
             "clocks": clk,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -149,7 +149,12 @@ int lee_read_probes(lee_ctx *ctx, double *host, long long *nrec);
  * stencil + stage-update kernel (step 6).  The first call captures one step in
  * a CUDA graph that later calls replay. */
 int lee_step(lee_ctx *ctx, long long nsteps);
-/* Wait for the bound stream. */
+/* Wait for the bound stream, then read the instance's status word: returns
+ * LEE_ERR_DIVERGED once a ghost pressure, ADE state or probe sample has been
+ * non-finite (checked on the device every stage), LEE_ERR_TIMEOUT if a stencil
+ * kernel gave up a bounded wait for a tile copy (the step is then incomplete).
+ * The status stays set until the state is rewritten (lee_write_state,
+ * lee_init_*). */
 int lee_sync(lee_ctx *ctx);
 
 /* ---- read back ------------------------------------------------------------ */
@@ -179,7 +184,9 @@ int lee_download_probes_async(lee_ctx *ctx, double *host, long long first, long 
 
 /* ---- test hooks ----------------------------------------------------------- */
 /* Ghost g of the plan: target node index (j*nx + i), boundary point, normal,
- * r = d/h, degree m, cloud size. meta = {bpx, bpy, nx, ny, r}. */
+ * r = d/h, degree m of the normal extrapolation (= the cloud-fit degree,
+ * 4 down to 1; a cloud whose nodes lie on one line takes the constant fit,
+ * its mean, with m = 1), cloud size. meta = {bpx, bpy, nx, ny, r}. */
 int lee_ghost_info(lee_ctx *ctx, int g, int *target, double *meta, int *m, int *ncloud);
 /* Cloud of ghost g: node indices and the combined FP64 weight rows
  * w[4*e + {0,1,2,3}] = {L0, w_p, w_d, w_f}; kappa = {kappa_p, kappa_u} such that
@@ -203,6 +210,12 @@ int lee_batch_bind(lee_batch *b, void *dev_ptr, long long dev_bytes, void *strea
 /* Advance every member nsteps steps. */
 int lee_batch_step(lee_batch *b, long long nsteps);
 const char *lee_batch_last_error(const lee_batch *b);
+/* Wait for the batch stream and copy every member's status word into
+ * host[0..n-1] (caller-owned, n = member count, member order = order of
+ * lee_batch_add): 0 = healthy, bit 0 = a bounded tile wait gave up (timeout),
+ * bit 1 = a ghost, ADE or probe value became non-finite (diverged).  One small
+ * gather kernel and one copy; LEE_ERR_ARG if n differs from the member count. */
+int lee_batch_status(lee_batch *b, long long *host, int n);
 /* Measurement hook: enqueue only one kernel of stage `stage` (1..4) for every
  * member: what = 0 ghost/ADE kernel, 1 stencil kernel.  Stages 2..4 read and
  * write disjoint buffers, so repeated launches are idempotent. */

@@ -28,7 +28,10 @@
  *   boundary mode of this closure.  Normal n points from the wall into the fluid;
  *   u_n (positive into the wall) = -u.n, so the Dirichlet datum for w = u.n is
  *   -u_n and the Neumann datum for dp/dn is +du_n/dt.  Critical damping uses
- *   the double-pole (Jordan) form of the same admittance.
+ *   the double-pole (Jordan) form of the same admittance.  A cloud clipped by
+ *   the domain edge lowers the fit degree k = m from 4 step by step; one that
+ *   cannot carry a plane (nodes on a single line) takes the constant fit (the
+ *   cloud mean) with a linear normal extrapolation (m = 1).
  * Parity unpinned: none of the functions below (each has a pin in the tests).
  */
 #include <math.h>
@@ -44,7 +47,8 @@ typedef struct {
     double bpx, bpy;            /* boundary point BP (Sec. 3.1)               */
     double nx, ny;              /* wall normal, wall -> fluid                 */
     double r;                   /* r = d / h, d = |GP - BP|                   */
-    int m;                      /* polynomial degree k = m actually used      */
+    int m;                      /* extrapolation degree m (= k, or 1 if k = 0) */
+    int k;                      /* degree of the cloud fit actually used       */
     int ncl;                    /* cloud size N                               */
     int cl[ORC_MAXCL];          /* cloud storage indices                      */
     double *L;                  /* (m+1) x ncl read-out rows at P_0..P_m      */
@@ -431,12 +435,20 @@ static int build_ghost(orc_t *o, orc_ghost *G, int gi, int gj)
     }
     G->ncl = N;
     /* degree k = m = 4; lowered step by step down to 1 when the cloud (clipped
-     * by the domain edge) cannot carry it */
+     * by the domain edge) cannot carry it.  A cloud that cannot carry even a
+     * plane (all its nodes on one line: a steep wall leaving the box) gets the
+     * constant fit, whose prediction is the cloud mean everywhere, and the
+     * normal extrapolation keeps m = 1 (L_0 = L_1 = 1/N). */
     int k;
     G->L = (double *)malloc(sizeof(double) * 5 * (N > 0 ? N : 1));
     for (k = 4; k >= 1; k--)
         if (lsq_rows(N, xp, yp, k, G->L) == 0) break;
-    if (k < 1) return 4;
+    G->k = k >= 1 ? k : 0;
+    if (k < 1) {
+        if (N < 1) return 4;
+        for (int e = 0; e < N; e++) G->L[e] = G->L[N + e] = 1.0 / N;
+        k = 1;
+    }
     G->m = k;
     /* Step 2 of Sec. 3.1: Lagrange factors along the normal.
      * Dirichlet / Neumann: nodes {-r, 1..m}, evaluated (value / slope) at s = 0.
@@ -495,7 +507,7 @@ int orc_setup(orc_t *o)
     }
     free(gs);
     o->n_reduced = 0;
-    for (int g = 0; g < ng; g++) o->n_reduced += o->g[g].m < 4;
+    for (int g = 0; g < ng; g++) o->n_reduced += o->g[g].k < 4;
     o->step = 0;
     if (bad) { snprintf(o->err, sizeof(o->err), "ghost setup failed (mask %d)", bad); return bad; }
     return 0;
@@ -505,6 +517,9 @@ int orc_n_ghost(orc_t *o) { return o->ng; }
 int orc_n_reduced(orc_t *o) { return o->n_reduced; }
 int orc_regime(orc_t *o) { return o->regime; }
 double orc_dt(orc_t *o) { return o->dt; }
+
+/* degree k of a ghost's cloud fit (0: constant fit, see build_ghost) */
+int orc_ghost_fit_degree(orc_t *o, int g) { return o->g[g].k; }
 
 void orc_ghost_meta(orc_t *o, int g, int *target, double *meta, int *m, int *ncl)
 {

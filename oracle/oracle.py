@@ -67,6 +67,7 @@ def _load():
             "orc_dt": (C.c_double, [vp]),
             "orc_ghost_meta": (None, [vp, C.c_int, _ip, _dp, _ip, _ip]),
             "orc_ghost_rows": (None, [vp, C.c_int, _ip, _dp, _dp, _dp, _dp]),
+            "orc_ghost_fit_degree": (C.c_int, [vp, C.c_int]),
             "orc_get_kind": (None, [vp, C.POINTER(C.c_ubyte)]),
             "orc_init_pulse": (None, [vp, C.c_double, C.c_double, C.c_double, C.c_double]),
             "orc_init_packet": (None, [vp] + [C.c_double] * 6),
@@ -202,7 +203,8 @@ class Oracle:
         return out.reshape(self.ny, self.nx)
 
     def ghost(self, g):
-        """Returns dict(target, bp, n, r, m, cloud, L ((m+1) x N), c, ct, ell)."""
+        """Returns dict(target, bp, n, r, m, k, cloud, L ((m+1) x N), c, ct, ell);
+        k is the degree of the cloud fit, m that of the normal extrapolation."""
         t = C.c_int(); m = C.c_int(); ncl = C.c_int()
         meta = np.empty(5)
         self._L.orc_ghost_meta(self._o, g, C.byref(t), _d(meta), C.byref(m), C.byref(ncl))
@@ -212,7 +214,7 @@ class Oracle:
         c = np.empty(5); ct = np.empty(5); ell = np.empty(5)
         self._L.orc_ghost_rows(self._o, g, cl.ctypes.data_as(_ip), _d(Lr), _d(c), _d(ct), _d(ell))
         return dict(target=t.value, bp=meta[0:2].copy(), n=meta[2:4].copy(), r=meta[4], m=mm,
-                    cloud=cl, L=Lr.reshape(mm + 1, N), c=c[:mm + 1], ct=ct[:mm + 1], ell=ell[:mm + 1])
+                    k=int(self._L.orc_ghost_fit_degree(self._o, g)), cloud=cl, L=Lr.reshape(mm + 1, N), c=c[:mm + 1], ct=ct[:mm + 1], ell=ell[:mm + 1])
 
     # state
     def init_pulse(self, xs, ys, amp, halfwidth):

@@ -91,6 +91,7 @@ struct lee_batch {
     cudaStream_t stream = nullptr;
     bool dirty = true;
     BatchView bv{};
+    long long *status = nullptr;      // device: members' status words (lee_batch_status)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     std::string err;
 };
@@ -252,6 +253,7 @@ BatchView single_view(lee_ctx *c) {
     bv.use_tma = c->hd.use_tma;
     bv.kernel_mode = c->hd.kernel_mode;
     bv.tile_w = c->hd.tile_w;
+    bv.tile_h = c->hd.tile_h;
     bv.probe_inst = c->dprefix + 4;
     bv.nprobe_inst = c->hd.np > 0 ? 1 : 0;
     bv.total_tiles = c->hd.ntiles;
@@ -434,6 +436,7 @@ int lee_bind(lee_ctx *ctx, void *dev_ptr, long long dev_bytes, void *stream) {
     d.tile_w = P.tile_w;
     d.per_x = ctx->g.bc_x == LEE_BC_PERIODIC; d.per_y = ctx->g.bc_y == LEE_BC_PERIODIC;
     d.h = ctx->g.h; d.inv_h = 1.0 / ctx->g.h; d.dt = ctx->g.cfl * ctx->g.h;
+    fill_stage_constants(d.dt, d.h, d.kf, d.kd);
     d.cx = 0.5 * (P.nx - 1); d.cy = 0.5 * (P.ny - 1);
     d.ng = ng;
     d.g_target = (const int *)(ctx->dev + L.gt);
@@ -537,7 +540,11 @@ int lee_step(lee_ctx *ctx, long long nsteps) {
 int lee_sync(lee_ctx *ctx) {
     if (!ctx) return LEE_ERR_ARG;
     if (!ctx->bound) return LEE_OK;
+    long long st = 0;
+    CK(cudaMemcpyAsync(&st, ctx->hd.clock + 2, sizeof st, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    if (st & (long long)STATUS_TIMEOUT) return fail(ctx, LEE_ERR_TIMEOUT, "a stencil kernel gave up waiting for a tile copy");
+    if (st & (long long)STATUS_DIVERGED) return fail(ctx, LEE_ERR_DIVERGED, "a ghost, ADE or probe value is not finite");
     return LEE_OK;
 }
 
@@ -632,6 +639,7 @@ int lee_write_state(lee_ctx *ctx, const void *blob) {
     const char *b = (const char *)blob;
     const size_t qb = 3 * (size_t)ctx->hd.plane * ctx->elem();
     CK(cudaMemcpyAsync(ctx->hd.clock, b, 16, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(ctx->hd.clock + 2, 0, sizeof(long long), ctx->stream));   // status: healthy
     CK(cudaMemcpyAsync(ctx->hd.q[0], b + 16, qb, cudaMemcpyHostToDevice, ctx->stream));
     if (ctx->hd.ng) {
         CK(cudaMemcpyAsync(ctx->hd.Xn, b + 16 + qb, 16 * (size_t)ctx->hd.ng, cudaMemcpyHostToDevice, ctx->stream));
@@ -650,6 +658,7 @@ int lee_upload_state_async(lee_ctx *ctx, const void *blob) {
     const char *b = (const char *)blob;
     const size_t qb = 3 * (size_t)ctx->hd.plane * ctx->elem();
     CK(cudaMemcpyAsync(ctx->hd.clock, b, 16, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(ctx->hd.clock + 2, 0, sizeof(long long), ctx->stream));   // status: healthy
     CK(cudaMemcpyAsync(ctx->hd.q[0], b + 16, qb, cudaMemcpyHostToDevice, ctx->stream));
     if (ctx->hd.ng) {
         CK(cudaMemcpyAsync(ctx->hd.Xn, b + 16 + qb, 16 * (size_t)ctx->hd.ng, cudaMemcpyHostToDevice, ctx->stream));
@@ -717,7 +726,8 @@ int lee_batch_add(lee_batch *b, lee_ctx *c) {
     if (!c->bound) { b->err = "context not bound"; return LEE_ERR_ARG; }
     if (c->g.precision != b->precision) { b->err = "precision differs from the batch"; return LEE_ERR_ARG; }
     if (!b->members.empty() && (b->members[0]->hd.kernel_mode != c->hd.kernel_mode ||
-                                b->members[0]->hd.tile_w != c->hd.tile_w)) {
+                                b->members[0]->hd.tile_w != c->hd.tile_w ||
+                                b->members[0]->hd.tile_h != c->hd.tile_h)) {
         b->err = "members use different stencil kernels (periodic axes or kernel selection): batch them separately";
         return LEE_ERR_ARG;
     }
@@ -741,7 +751,7 @@ static long long batch_bytes(const lee_batch *b) {
     size_t nch = 1, nst = 1;
     for (auto *c : b->members) { nch += n_chunks(c->hd.ng); nst += (size_t)c->hd.tiles_x * c->hd.tiles_y; }
     return (long long)(align_up(n * sizeof(InstDesc)) + 2 * align_up((n + 1) * 4) + align_up(nch * sizeof(int4)) +
-                       align_up(nst * sizeof(int4)));
+                       align_up(nst * sizeof(int4)) + align_up(n * sizeof(long long)));
 }
 
 int lee_batch_plan(lee_batch *b, long long *device_bytes) {
@@ -783,7 +793,9 @@ static int batch_refresh(lee_batch *b) {
     const int nstrips = (int)strips.size();
     strips.resize(std::max<size_t>(strips.size(), 1));
     const size_t o_desc = 0, o_tp = align_up(n * sizeof(InstDesc)), o_pi = o_tp + align_up((n + 1) * 4),
-                 o_ch = o_pi + align_up((n + 1) * 4), o_st = o_ch + align_up(chunks.size() * sizeof(int4));
+                 o_ch = o_pi + align_up((n + 1) * 4), o_st = o_ch + align_up(chunks.size() * sizeof(int4)),
+                 o_status = o_st + align_up(strips.size() * sizeof(int4));
+    b->status = (long long *)(b->dev + o_status);
     cudaError_t e;
     if (n) {
         if ((e = cudaMemcpyAsync(b->dev + o_desc, descs.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice, b->stream)) ||
@@ -807,6 +819,7 @@ static int batch_refresh(lee_batch *b) {
     bv.use_tma = n ? descs[0].use_tma : 0;
     bv.kernel_mode = n ? descs[0].kernel_mode : KERNEL_SMEM;
     bv.tile_w = n ? descs[0].tile_w : TILE_X;
+    bv.tile_h = n ? descs[0].tile_h : TILE_Y;
     bv.probe_inst = (const int *)(b->dev + o_pi);
     bv.nprobe_inst = 0;
     for (auto *c : b->members) bv.nprobe_inst += c->hd.np > 0;
@@ -828,6 +841,25 @@ int lee_batch_step(lee_batch *b, long long nsteps) {
     if (b->members.empty() || nsteps <= 0) return LEE_OK;
     cudaError_t e = run_steps(b->bv, nsteps, b->stream, b->graph);
     if (e != cudaSuccess) { b->err = std::string("batch step: ") + cudaGetErrorString(e); return LEE_ERR_CUDA; }
+    return LEE_OK;
+}
+
+int lee_batch_status(lee_batch *b, long long *host, int n) {
+    if (!b || (n > 0 && !host)) return LEE_ERR_ARG;
+    if (!b->dev) { b->err = "batch not bound"; return LEE_ERR_ARG; }
+    if (n != (int)b->members.size()) { b->err = "n differs from the member count"; return LEE_ERR_ARG; }
+    if (b->dirty) {
+        int rc = batch_refresh(b);
+        if (rc != LEE_OK) return rc;
+    }
+    if (n == 0) return LEE_OK;
+    cudaError_t e;
+    if ((e = launch_status_gather(b->bv, b->status, b->stream)) ||
+        (e = cudaMemcpyAsync(host, b->status, (size_t)n * sizeof(long long), cudaMemcpyDeviceToHost, b->stream)) ||
+        (e = cudaStreamSynchronize(b->stream))) {
+        b->err = std::string("batch status: ") + cudaGetErrorString(e);
+        return LEE_ERR_CUDA;
+    }
     return LEE_OK;
 }
 

@@ -26,6 +26,10 @@ constexpr int HALO = 4;                 // smem halo on each side (7-pt DRP need
                                         // the 5-pt band stencils at the last row need 4)
 constexpr int MAX_PROBES = 1024;
 
+// status word of an instance (InstDesc::clock[2]), set on the device
+constexpr unsigned long long STATUS_TIMEOUT = 1ull;    // a bounded wait for a tile copy gave up
+constexpr unsigned long long STATUS_DIVERGED = 2ull;   // a ghost, ADE or probe value is not finite
+
 // tile flags
 constexpr uint32_t TILE_BAND = 1u;      // output region meets the 3 outer layers
 constexpr uint32_t TILE_MIXED = 2u;     // has non-fluid or out-of-grid outputs
@@ -37,6 +41,12 @@ constexpr uint32_t TILE_SPONGE = 4u;    // meets the absorbing ramp along the ou
 // slowly growing mode of the one-sided/radiation closure on large domains.
 constexpr int SPONGE_W = 12;
 constexpr double SPONGE_K = 0.04;
+
+// Per-stage constants of the bulk update of stage k (Sec. 3.2 step 6, Eq. 3):
+// alpha_k dt, alpha_k dt a_j / h (j = 1..3), alpha_k dt SPONGE_K / h, 1 / h,
+// SPONGE_K / h.
+enum { K_AD = 0, K_K1 = 1, K_K2 = 2, K_K3 = 3, K_KS = 4, K_INVH = 5, K_SK = 6 };
+void fill_stage_constants(double dt, double h, float kf[4][8], double kd[4][8]);
 
 // Combined FP64 weight row entry of one cloud node: p_BP = sum l0 p,
 // Neumann row wp, Dirichlet row wd, free-extrapolation row wf.
@@ -66,6 +76,10 @@ struct InstDesc {
     double *Xn;                 // ng x 2 ADE state at t_n
     double *Xs;                 // ng x 2 ADE state of the current stage
     double A[4], b[2], c[2];    // X' = A X + b p_BP, u_n = c . X
+    // per-stage constants of the bulk update (index K_*), computed on the host
+    // in FP64 so that no kernel does FP64 arithmetic per tile
+    float kf[4][8];
+    double kd[4][8];
     // monopole source (Sec. 4.3): s = amp * sigma_k * gx[i] * gy[j]
     double s_amp, s_omega;
     double G_re[4], G_im[4];    // stage k: sigma = sin(w t_n) G_re + cos(w t_n) G_im
@@ -133,7 +147,7 @@ struct BatchView {
     int nstrips;
     int use_tma;
     int kernel_mode;
-    int tile_w;
+    int tile_w, tile_h;
     const int *probe_inst;      // instances with probes (device), nprobe_inst entries
     int nprobe_inst;
     int total_tiles;
@@ -153,6 +167,7 @@ cudaError_t launch_init(const InstDesc *dinst, const InstDesc &h, int kind, cons
 cudaError_t launch_to_staging(const InstDesc *dinst, const InstDesc &h, int which, int buf, cudaStream_t s);
 cudaError_t launch_from_staging(const InstDesc *dinst, const InstDesc &h, int which, cudaStream_t s);
 cudaError_t launch_energy(const InstDesc *dinst, const InstDesc &h, cudaStream_t s);
+cudaError_t launch_status_gather(const BatchView &bv, long long *out, cudaStream_t s);
 long long launch_count();
 void count_launch(int n = 1);
 // message for lee_last_error(NULL) (entry points without a context)

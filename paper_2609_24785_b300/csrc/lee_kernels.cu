@@ -29,7 +29,6 @@ std::atomic<long long> g_launches{0};
 long long launch_count() { return g_launches.load(); }
 void count_launch(int n) { g_launches += n; }
 
-__constant__ double c_alpha[4] = {0.25, 1.0 / 3.0, 0.5, 1.0};
 
 // DRP coefficients of Sec. 2.2 (a_{-k} = -a_k)
 template <typename T> struct Drp;
@@ -139,11 +138,15 @@ ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int4 *__restric
     U[t] = (T)(wg * n.x - tg * n.y);
     V[t] = (T)(wg * n.y + tg * n.x);
     // ADE stage update X(k) = X(n) + alpha_k dt X'
-    const double ad = c_alpha[stage - 1] * d.dt;
+    const double ad = d.kd[stage - 1][K_AD];
     const double y0 = xn0 + ad * xd0, y1 = xn1 + ad * xd1;
     d.Xs[2 * g] = y0;
     d.Xs[2 * g + 1] = y1;
     if (stage == 4) { d.Xn[2 * g] = y0; d.Xn[2 * g + 1] = y1; }
+    // divergence: every stage reads the field at the wall, so a non-finite
+    // wall pressure or ADE state is flagged within the stage it appears
+    if (!(isfinite(pbp) && isfinite(y0) && isfinite(y1)))
+        atomicOr((unsigned long long *)&d.clock[2], STATUS_DIVERGED);
 }
 
 // ---------------------------------------------------------------- stencil
@@ -151,7 +154,6 @@ ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int4 *__restric
 constexpr int BOX_X = TILE_X + 2 * HALO;                    // 72
 constexpr int THREADS_X = TILE_X / 4;                       // 16 threads across, 4 columns each
 constexpr int RY = 4;                                       // rows per thread (shared-memory kernel)
-constexpr int LIST_CAP = 1024;                              // band points per tile (<= 3 (64 + 64))
 
 template <typename T> struct alignas(4 * sizeof(T)) Vec4 { T v[4]; };
 
@@ -178,14 +180,24 @@ __device__ __forceinline__ T deriv_general(F f, int x, int n, int per, T inv_h) 
 }
 
 // ((W - d) / W)^2 of the absorbing ramp at node (gx, gy), 0 outside it
+// (FP32: times the rounded 1 / W instead of a division)
 template <typename T>
 __device__ __forceinline__ T ramp2(const InstDesc &d, int gx, int gy) {
     int dist = 1 << 30;
     if (!d.per_x) dist = min(dist, min(gx, d.nx - 1 - gx));
     if (!d.per_y) dist = min(dist, min(gy, d.ny - 1 - gy));
     if (dist >= SPONGE_W) return T(0);
-    const T r = (T)(SPONGE_W - dist) / (T)SPONGE_W;
+    const T r = sizeof(T) == 4 ? (T)(SPONGE_W - dist) * (T)(1.0f / SPONGE_W) : (T)(SPONGE_W - dist) / (T)SPONGE_W;
     return r * r;
+}
+
+// the per-stage constants of an instance in the bulk precision
+template <typename T> __device__ __forceinline__ const T *stage_k(const InstDesc &d, int stage);
+template <> __device__ __forceinline__ const float *stage_k<float>(const InstDesc &d, int stage) {
+    return d.kf[stage - 1];
+}
+template <> __device__ __forceinline__ const double *stage_k<double>(const InstDesc &d, int stage) {
+    return d.kd[stage - 1];
 }
 
 __device__ __forceinline__ double stage_sigma(const InstDesc &d, int stage) {
@@ -203,92 +215,169 @@ template <typename T> struct QnSrc {
     __device__ __forceinline__ long long at(int x, int y) const { return (long long)y * stride + x; }
 };
 
+// Paired FP32 arithmetic (two lanes per instruction); a - b is the FMA
+// b * (-1) + a, which rounds once like a subtraction.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 pair(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+
+// One fluid node of the three outer layers: one-sided stencils (rows 0..2
+// from an edge) and the radiation condition
+// dq/dt = -(cos th dq/dx + sin th dq/dy + q / (2 rho)), polar about the domain
+// centre, plus the ramp term.  (lx, ly) is tile-local; the box around the tile
+// holds HALO nodes on every side, enough for the 5-point one-sided rows.
+template <typename T>
+__device__ __forceinline__ void band_point(const T *sp, const T *su, const T *sv, const int bs, const QnSrc<T> &qn,
+                                           const InstDesc &d, T *out, int gx, int gy, int lx, int ly, const T *K) {
+    const T inv_h = K[K_INVH], half_inv_h = T(0.5) * inv_h;
+    const T ad = K[K_AD], sk_h = K[K_SK];
+    const int sr = HALO + ly, sc = HALO + lx;
+    auto fxp = [&](int q) { return sp[sr * bs + sc + q]; };
+    auto fxu = [&](int q) { return su[sr * bs + sc + q]; };
+    auto fxv = [&](int q) { return sv[sr * bs + sc + q]; };
+    auto fyp = [&](int q) { return sp[(sr + q) * bs + sc]; };
+    auto fyu = [&](int q) { return su[(sr + q) * bs + sc]; };
+    auto fyv = [&](int q) { return sv[(sr + q) * bs + sc]; };
+    const T dpdx = deriv_general<T>(fxp, gx, d.nx, d.per_x, inv_h);
+    const T dpdy = deriv_general<T>(fyp, gy, d.ny, d.per_y, inv_h);
+    const T dudx = deriv_general<T>(fxu, gx, d.nx, d.per_x, inv_h);
+    const T dudy = deriv_general<T>(fyu, gy, d.ny, d.per_y, inv_h);
+    const T dvdx = deriv_general<T>(fxv, gx, d.nx, d.per_x, inv_h);
+    const T dvdy = deriv_general<T>(fyv, gy, d.ny, d.per_y, inv_h);
+    const T rx = T(gx) - (T)d.cx, ryy = T(gy) - (T)d.cy;
+    const T rho = sqrt(rx * rx + ryy * ryy);
+    const T ct = rx / rho, st = ryy / rho;
+    const T q2 = half_inv_h / rho;                               // 1 / (2 h rho)
+    const T sg = sk_h * ramp2<T>(d, gx, gy);
+    const T p0 = sp[sr * bs + sc], u0 = su[sr * bs + sc], v0 = sv[sr * bs + sc];
+    const T rp = -(ct * dpdx + st * dpdy + p0 * q2) - sg * p0;
+    const T ru = -(ct * dudx + st * dudy + u0 * q2) - sg * u0;
+    const T rv = -(ct * dvdx + st * dvdy + v0 * q2) - sg * v0;
+    const long long o = (long long)gy * d.pitch + gx, plane = d.plane;
+    const long long oq = qn.at(lx, ly);
+    out[o] = qn.p[oq] + ad * rp;
+    out[plane + o] = qn.u[oq] + ad * ru;
+    out[2 * plane + o] = qn.v[oq] + ad * rv;
+}
+
 // Step 6 of Sec. 3.2 on one tile: stage update of every output node owned by
 // this thread (4 columns x RY rows).  sp, su, sv point at the box origin
 // (tile origin - HALO in x and y) of Q(k-1), bs elements per row: a shared-
-// memory halo box, or global memory for interior tiles.  Interior fluid nodes take the vector
-// DRP path; non-fluid nodes get zeros; fluid nodes of the three outer layers
-// are appended to `list` and done afterwards by band_points().
-//   FOLD: FP32 form q - sum_j k_j (f_{+j} - f_{-j}), k_j = alpha dt a_j / h;
-//   else: q + alpha dt RHS with RHS from the DRP derivatives times 1/h.
-template <typename T, bool FOLD, int RY>
-__device__ __forceinline__ void tile_points(const T *sp, const T *su, const T *sv, long long bs, const QnSrc<T> &qn,
-                                            const InstDesc &d, T *out, int xt, int yt, uint32_t flags, int stage,
-                                            T src, int txi, int tyi, unsigned short *list, int *list_n) {
+// memory halo box, or global memory for interior tiles.  FL is the tile's
+// flags, fixed at compile time so that an interior tile (FL == 0) runs the
+// DRP update alone:
+//   TILE_MIXED: node kinds from the mask; non-fluid nodes get zeros, nodes
+//     beyond nx or ny are skipped;
+//   TILE_BAND: fluid nodes of the three outer layers are appended to the
+//     warp's list (wl_idx, wl_n in shared memory) and then done by the warp's
+//     32 lanes together (band_point); no block-wide barrier is involved;
+//   TILE_SPONGE: the absorbing-ramp term.
+// FP32 (folded form, Eq. 3 with the constants combined):
+//   q = q^n - sum_j k_j (f_{+j} - f_{-j}),  k_j = alpha dt a_j / h,
+// evaluated two columns per instruction; FP64: q = q^n + alpha dt RHS with
+// the DRP derivatives times 1/h.
+// QNG: Q^n is in global memory (FP32 then loads it into registers first).
+template <typename T, int RY, int FL, bool QNG>
+__device__ __forceinline__ void tile_points(const T *sp, const T *su, const T *sv, const int bs, const QnSrc<T> &qn,
+                                            const InstDesc &d, T *out, int xt, int yt, const T *K, T src, int txi,
+                                            int tyi, unsigned short *wl_idx, int *wl_n) {
+    constexpr bool MIXED = (FL & TILE_MIXED) != 0, BAND = (FL & TILE_BAND) != 0, SPONGE = (FL & TILE_SPONGE) != 0;
+    constexpr bool FOLD = sizeof(T) == 4;
     const int cx0 = HALO + 4 * txi, ry0 = HALO + RY * tyi;     // box coordinates of the first output
     const int lx0 = 4 * txi, ly0 = RY * tyi;                   // tile-local
     const int gx0 = xt + lx0, gy0 = yt + ly0;
-    const int nx = d.nx, ny = d.ny, pitch = d.pitch;
+    // only mixed tiles reach past the last column or row; threads there stay
+    // for the warp's band pass
+    const bool live = !MIXED || (gx0 < d.nx && gy0 < d.ny);
+    if (live) {
+    const int pitch = d.pitch;
     const long long plane = d.plane;
-    const T ad = (T)(c_alpha[stage - 1] * d.dt);
-    const T inv_h = (T)d.inv_h;
-    const double adh = c_alpha[stage - 1] * d.dt * d.inv_h;
-    const T k1 = (T)(adh * 0.770882380518), k2 = (T)(adh * -0.166705904415), k3 = (T)(adh * 0.020843142770);
-    const T ksp = (T)(adh * SPONGE_K);            // alpha dt (SPONGE_K / h), folded form
-    const T sk_h = (T)(SPONGE_K * d.inv_h);       // SPONGE_K / h
-    const T *gxs = (const T *)d.gx;
-    const T *gys = (const T *)d.gy;
-    if (gx0 >= nx || gy0 >= ny) return;
+    const T ad = K[K_AD], inv_h = K[K_INVH];
+    const T k1 = K[K_K1], k2 = K[K_K2], k3 = K[K_K3];
+    const T ksp = K[K_KS];                        // alpha dt (SPONGE_K / h), folded form
+    const T sk_h = K[K_SK];                       // SPONGE_K / h
 
     // FP32: this thread's Q^n rows are loaded first so that their latency
     // overlaps the shared-memory work below (FP64 loads them row by row to
     // keep its registers)
-    constexpr bool PRELOAD = sizeof(T) == 4;
+    constexpr bool PRELOAD = sizeof(T) == 4 && QNG;
     Vec4<T> qn0[PRELOAD ? RY : 1], qn1[PRELOAD ? RY : 1], qn2[PRELOAD ? RY : 1];
     if (PRELOAD) {
 #pragma unroll
         for (int r = 0; r < RY; ++r)
-            if (gy0 + r < ny) {
+            if (!MIXED || gy0 + r < d.ny) {
                 qn0[r] = ld4(qn.p + qn.at(lx0, ly0 + r));
                 qn1[r] = ld4(qn.u + qn.at(lx0, ly0 + r));
                 qn2[r] = ld4(qn.v + qn.at(lx0, ly0 + r));
             }
     }
-    // y differences of p and v on the thread's 4 columns
-    T dpy[RY][4], dvy[RY][4], vc[RY][4];
+    // y differences from the thread's 4 columns of p and v (rows -3 .. RY + 2
+    // around its outputs), done first so that the column window dies early:
+    //   FP32: yv = alpha dt dp/dy, yp = alpha dt dv/dy, two columns per pair;
+    //   FP64: dpy = dp/dy, dvy = dv/dy
+    float2 yv[FOLD ? RY : 1][2], yp[FOLD ? RY : 1][2];
+    T dpy[FOLD ? 1 : RY][4], dvy[FOLD ? 1 : RY][4];
+    T vc[SPONGE ? RY : 1][4];                          // v at the outputs (ramp term)
     {
-        T cp[RY + 6][4], cv[RY + 6][4];
+        Vec4<T> cp[RY + 6], cv[RY + 6];
 #pragma unroll
         for (int r = 0; r < RY + 6; ++r) {
-            const Vec4<T> a = ld4(sp + (ry0 - 3 + r) * bs + cx0);
-            const Vec4<T> c = ld4(sv + (ry0 - 3 + r) * bs + cx0);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) { cp[r][q] = a.v[q]; cv[r][q] = c.v[q]; }
+            cp[r] = ld4(sp + (ry0 - 3 + r) * bs + cx0);
+            cv[r] = ld4(sv + (ry0 - 3 + r) * bs + cx0);
         }
 #pragma unroll
-        for (int r = 0; r < RY; ++r)
+        for (int r = 0; r < RY; ++r) {
+            if constexpr (FOLD) {
+                const float2 K1 = dup2(k1), K2 = dup2(k2), K3 = dup2(k3);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                vc[r][q] = cv[r + 3][q];
-                if (FOLD) {
-                    dpy[r][q] = k1 * (cp[r + 4][q] - cp[r + 2][q]) + k2 * (cp[r + 5][q] - cp[r + 1][q]) +
-                                k3 * (cp[r + 6][q] - cp[r][q]);
-                    dvy[r][q] = k1 * (cv[r + 4][q] - cv[r + 2][q]) + k2 * (cv[r + 5][q] - cv[r + 1][q]) +
-                                k3 * (cv[r + 6][q] - cv[r][q]);
-                } else {
-                    dpy[r][q] = drp<T>(cp[r][q], cp[r + 1][q], cp[r + 2][q], cp[r + 4][q], cp[r + 5][q], cp[r + 6][q]) * inv_h;
-                    dvy[r][q] = drp<T>(cv[r][q], cv[r + 1][q], cv[r + 2][q], cv[r + 4][q], cv[r + 5][q], cv[r + 6][q]) * inv_h;
+                for (int P = 0; P < 2; ++P) {
+                    auto col = [&](const Vec4<T> &v) { return pair(v.v[2 * P], v.v[2 * P + 1]); };
+                    float2 a = __fmul2_rn(K3, sub2(col(cp[r + 6]), col(cp[r])));
+                    a = __ffma2_rn(K2, sub2(col(cp[r + 5]), col(cp[r + 1])), a);
+                    yv[r][P] = __ffma2_rn(K1, sub2(col(cp[r + 4]), col(cp[r + 2])), a);
+                    float2 c = __fmul2_rn(K3, sub2(col(cv[r + 6]), col(cv[r])));
+                    c = __ffma2_rn(K2, sub2(col(cv[r + 5]), col(cv[r + 1])), c);
+                    yp[r][P] = __ffma2_rn(K1, sub2(col(cv[r + 4]), col(cv[r + 2])), c);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    dpy[r][q] = drp<T>(cp[r].v[q], cp[r + 1].v[q], cp[r + 2].v[q], cp[r + 4].v[q], cp[r + 5].v[q],
+                                       cp[r + 6].v[q]) * inv_h;
+                    dvy[r][q] = drp<T>(cv[r].v[q], cv[r + 1].v[q], cv[r + 2].v[q], cv[r + 4].v[q], cv[r + 5].v[q],
+                                       cv[r + 6].v[q]) * inv_h;
                 }
             }
+            if (SPONGE) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) vc[r][q] = cv[r + 3].v[q];
+            }
+        }
+    }
+    T gxv[4] = {T(0), T(0), T(0), T(0)};
+    if (src != T(0)) {
+        const T *gxs = (const T *)d.gx;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) gxv[q] = gx0 + q < d.nx ? gxs[gx0 + q] : T(0);
     }
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
         const int gy = gy0 + r;
-        if (gy >= ny) break;
-        // node categories: 0 interior fluid, 1 non-fluid (zero), 2 band fluid (list), 3 outside
+        if (MIXED && gy >= d.ny) break;
+        // node categories: 0 interior fluid, 1 non-fluid (zero), 2 band fluid, 3 outside
         int cat[4] = {0, 0, 0, 0};
         bool simple = true;
-        if (flags) {
+        if (MIXED || BAND) {
             uchar4 kind = make_uchar4(1, 1, 1, 1);
-            if (flags & TILE_MIXED) kind = *reinterpret_cast<const uchar4 *>(d.mask + (long long)gy * pitch + gx0);
+            if (MIXED) kind = *reinterpret_cast<const uchar4 *>(d.mask + (long long)gy * pitch + gx0);
             const unsigned char kk[4] = {kind.x, kind.y, kind.z, kind.w};
-            const bool yband = !d.per_y && (gy < 3 || gy > ny - 4);
+            const bool yband = BAND && !d.per_y && (gy < 3 || gy > d.ny - 4);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int gx = gx0 + q;
-                if (gx >= nx) cat[q] = 3;
-                else if (kk[q] != 1) cat[q] = 1;
-                else if (yband || (!d.per_x && (gx < 3 || gx > nx - 4))) cat[q] = 2;
+                if (MIXED && gx >= d.nx) cat[q] = 3;
+                else if (MIXED && kk[q] != 1) cat[q] = 1;
+                else if (BAND && (yband || (!d.per_x && (gx < 3 || gx > d.nx - 4)))) cat[q] = 2;
                 simple = simple && cat[q] == 0;
             }
         }
@@ -308,34 +397,51 @@ __device__ __forceinline__ void tile_points(const T *sp, const T *su, const T *s
             n1 = ld4(qn.u + qn.at(lx0, ly0 + r));
             n2 = ld4(qn.v + qn.at(lx0, ly0 + r));
         }
-        const T sy = src != T(0) ? src * gys[gy] : T(0);
-        Vec4<T> o0, o1, o2;
+        // absorbing ramp ((W - d) / W)^2 of the thread's 4 nodes
+        T rr[4] = {T(0), T(0), T(0), T(0)};
+        if (SPONGE) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int c = 4 + q;
-            // absorbing ramp: rate (SPONGE_K / h) ramp2
-            const T rr = (flags & TILE_SPONGE) ? ramp2<T>(d, gx0 + q, gy) : T(0);
-            if (FOLD) {
-                const T dpx = k1 * (wp[c + 1] - wp[c - 1]) + k2 * (wp[c + 2] - wp[c - 2]) + k3 * (wp[c + 3] - wp[c - 3]);
-                const T dux = k1 * (wu[c + 1] - wu[c - 1]) + k2 * (wu[c + 2] - wu[c - 2]) + k3 * (wu[c + 3] - wu[c - 3]);
-                T op = n0.v[q] - (dux + dvy[r][q]);
-                if (src != T(0)) op += ad * sy * gxs[gx0 + q];
-                T ou = n1.v[q] - dpx, ov = n2.v[q] - dpy[r][q];
-                if (rr != T(0)) {
-                    const T ks = ksp * rr;
-                    op -= ks * wp[c]; ou -= ks * wu[c]; ov -= ks * vc[r][q];
+            for (int q = 0; q < 4; ++q) rr[q] = ramp2<T>(d, gx0 + q, gy);
+        }
+        const T sy = src != T(0) ? src * ((const T *)d.gy)[gy] : T(0);
+        Vec4<T> o0, o1, o2;
+        if constexpr (FOLD) {
+            const float2 K1 = dup2(k1), K2 = dup2(k2), K3 = dup2(k3);
+#pragma unroll
+            for (int P = 0; P < 2; ++P) {
+                const int c = 4 + 2 * P;                       // window index of the pair's first column
+                auto col = [&](const Vec4<T> &v) { return pair(v.v[2 * P], v.v[2 * P + 1]); };
+                // alpha dt dp/dx
+                float2 au = __fmul2_rn(K3, pair(wp[c + 3] - wp[c - 3], wp[c + 4] - wp[c - 2]));
+                au = __ffma2_rn(K2, pair(wp[c + 2] - wp[c - 2], wp[c + 3] - wp[c - 1]), au);
+                au = __ffma2_rn(K1, pair(wp[c + 1] - wp[c - 1], wp[c + 2] - wp[c]), au);
+                // alpha dt (du/dx + dv/dy)
+                float2 ap = __ffma2_rn(K3, pair(wu[c + 3] - wu[c - 3], wu[c + 4] - wu[c - 2]), yp[r][P]);
+                ap = __ffma2_rn(K2, pair(wu[c + 2] - wu[c - 2], wu[c + 3] - wu[c - 1]), ap);
+                ap = __ffma2_rn(K1, pair(wu[c + 1] - wu[c - 1], wu[c + 2] - wu[c]), ap);
+                float2 op = sub2(col(n0), ap), ou = sub2(col(n1), au), ov = sub2(col(n2), yv[r][P]);
+                if (SPONGE) {
+                    const float2 ks = pair(-ksp * rr[2 * P], -ksp * rr[2 * P + 1]);
+                    op = __ffma2_rn(ks, pair(wp[c], wp[c + 1]), op);
+                    ou = __ffma2_rn(ks, pair(wu[c], wu[c + 1]), ou);
+                    ov = __ffma2_rn(ks, pair(vc[r][2 * P], vc[r][2 * P + 1]), ov);
                 }
-                o0.v[q] = op;
-                o1.v[q] = ou;
-                o2.v[q] = ov;
-            } else {
+                if (src != T(0)) op = __ffma2_rn(dup2(ad * sy), pair(gxv[2 * P], gxv[2 * P + 1]), op);
+                o0.v[2 * P] = op.x; o0.v[2 * P + 1] = op.y;
+                o1.v[2 * P] = ou.x; o1.v[2 * P + 1] = ou.y;
+                o2.v[2 * P] = ov.x; o2.v[2 * P + 1] = ov.y;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int c = 4 + q;
                 const T dpdx = drp<T>(wp[c - 3], wp[c - 2], wp[c - 1], wp[c + 1], wp[c + 2], wp[c + 3]) * inv_h;
                 const T dudx = drp<T>(wu[c - 3], wu[c - 2], wu[c - 1], wu[c + 1], wu[c + 2], wu[c + 3]) * inv_h;
                 T rp = -(dudx + dvy[r][q]);
-                if (src != T(0)) rp += sy * gxs[gx0 + q];
+                if (src != T(0)) rp += sy * gxv[q];
                 T ru = -dpdx, rv = -dpy[r][q];
-                if (rr != T(0)) {
-                    const T sg = sk_h * rr;
+                if (SPONGE && rr[q] != T(0)) {
+                    const T sg = sk_h * rr[q];
                     rp -= sg * wp[c]; ru -= sg * wu[c]; rv -= sg * vc[r][q];
                 }
                 o0.v[q] = n0.v[q] + ad * rp;
@@ -356,55 +462,50 @@ __device__ __forceinline__ void tile_points(const T *sp, const T *su, const T *s
                 } else if (cat[q] == 1) {
                     out[o + q] = T(0); out[plane + o + q] = T(0); out[2 * plane + o + q] = T(0);
                 } else if (cat[q] == 2) {
-                    const int slot = atomicAdd(list_n, 1);
-                    if (slot < LIST_CAP) list[slot] = (unsigned short)(((ly0 + r) << 8) | (lx0 + q));
+                    // at most 4 RY entries per thread, 128 RY per warp
+                    wl_idx[atomicAdd(wl_n, 1)] = (unsigned short)(((ly0 + r) << 8) | (lx0 + q));
                 }
             }
         }
     }
-}
-
-// Fluid nodes of the three outer layers listed by tile_points(): one-sided
-// stencils (rows 0..2) and the radiation condition
-// dq/dt = -(cos th dq/dx + sin th dq/dy + q / (2 rho)), polar about the centre.
-template <typename T>
-__device__ __forceinline__ void band_points(const T *sp, const T *su, const T *sv, int bs, const QnSrc<T> &qn,
-                                            const InstDesc &d, T *out, int xt, int yt, int stage,
-                                            const unsigned short *list, int n, int tid, int nthreads) {
-    const T inv_h = (T)d.inv_h, half_inv_h = T(0.5) * inv_h;
-    const T ad = (T)(c_alpha[stage - 1] * d.dt);
-    const long long plane = d.plane;
-    for (int i = tid; i < n; i += nthreads) {
-        const int lx = list[i] & 0xff, ly = list[i] >> 8;
-        const int gx = xt + lx, gy = yt + ly;
-        const int sr = HALO + ly, sc = HALO + lx;
-        auto fxp = [&](int q) { return sp[sr * bs + sc + q]; };
-        auto fxu = [&](int q) { return su[sr * bs + sc + q]; };
-        auto fxv = [&](int q) { return sv[sr * bs + sc + q]; };
-        auto fyp = [&](int q) { return sp[(sr + q) * bs + sc]; };
-        auto fyu = [&](int q) { return su[(sr + q) * bs + sc]; };
-        auto fyv = [&](int q) { return sv[(sr + q) * bs + sc]; };
-        const T dpdx = deriv_general<T>(fxp, gx, d.nx, d.per_x, inv_h);
-        const T dpdy = deriv_general<T>(fyp, gy, d.ny, d.per_y, inv_h);
-        const T dudx = deriv_general<T>(fxu, gx, d.nx, d.per_x, inv_h);
-        const T dudy = deriv_general<T>(fyu, gy, d.ny, d.per_y, inv_h);
-        const T dvdx = deriv_general<T>(fxv, gx, d.nx, d.per_x, inv_h);
-        const T dvdy = deriv_general<T>(fyv, gy, d.ny, d.per_y, inv_h);
-        const T rx = T(gx) - (T)d.cx, ryy = T(gy) - (T)d.cy;
-        const T rho = sqrt(rx * rx + ryy * ryy);
-        const T ct = rx / rho, st = ryy / rho;
-        const T q2 = half_inv_h / rho;                               // 1 / (2 h rho)
-        const T sg = (T)(SPONGE_K * d.inv_h) * ramp2<T>(d, gx, gy);
-        const T rp = -(ct * dpdx + st * dpdy + sp[sr * bs + sc] * q2) - sg * sp[sr * bs + sc];
-        const T ru = -(ct * dudx + st * dudy + su[sr * bs + sc] * q2) - sg * su[sr * bs + sc];
-        const T rv = -(ct * dvdx + st * dvdy + sv[sr * bs + sc] * q2) - sg * sv[sr * bs + sc];
-        const long long o = (long long)gy * d.pitch + gx;
-        const long long oq = qn.at(lx, ly);
-        out[o] = qn.p[oq] + ad * rp;
-        out[plane + o] = qn.u[oq] + ad * ru;
-        out[2 * plane + o] = qn.v[oq] + ad * rv;
+    }  // live
+    if (BAND) {
+        __syncwarp();
+        const int n = *(volatile int *)wl_n;
+        for (int i = threadIdx.x & 31; i < n; i += 32) {
+            const int e = wl_idx[i], lx = e & 0xff, ly = e >> 8;
+            band_point<T>(sp, su, sv, bs, qn, d, out, xt + lx, yt + ly, lx, ly, K);
+        }
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) *wl_n = 0;
+        __syncwarp();
     }
 }
+
+// tile_points() with the tile's flags as a compile-time parameter: interior
+// tiles get their own code, every other tile the general form (all flags set
+// is a superset: each node is classified from the mask, its indices and the
+// ramp).  More variants would push the 128-register TMA kernel into spills.
+template <typename T, int RY, bool QNG>
+__device__ __forceinline__ void tile_dispatch(uint32_t flags, const T *sp, const T *su, const T *sv, const int bs,
+                                              const QnSrc<T> &qn, const InstDesc &d, T *out, int xt, int yt,
+                                              const T *K, T src, int txi, int tyi, unsigned short *wl_idx,
+                                              int *wl_n) {
+    if (flags == 0)
+        tile_points<T, RY, 0, QNG>(sp, su, sv, bs, qn, d, out, xt, yt, K, src, txi, tyi, wl_idx, wl_n);
+    else
+        tile_points<T, RY, TILE_BAND | TILE_MIXED | TILE_SPONGE, QNG>(sp, su, sv, bs, qn, d, out, xt, yt, K, src,
+                                                                      txi, tyi, wl_idx, wl_n);
+}
+
+// per-warp band lists: 128 RY entries per warp, zeroed counters
+template <int NWARP, int RY> struct WarpLists {
+    unsigned short idx[NWARP][128 * RY];
+    int n[NWARP];
+    __device__ __forceinline__ void init() {
+        for (int w = threadIdx.x; w < NWARP; w += blockDim.x) n[w] = 0;
+    }
+};
 
 // ---- shared-memory kernel (FP64, periodic instances): 64 x 32 tiles,
 // threads load the halo box, Q^n is read from global memory
@@ -423,10 +524,12 @@ stencil_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__restri
     T *su = sp + SY * BOX_X;
     T *sv = su + SY * BOX_X;
     __shared__ T s_src;
-    __shared__ unsigned short list[LIST_CAP];
-    __shared__ int list_n;
+    __shared__ WarpLists<STENCIL_THREADS / 32, RY> wl;
+    wl.init();
+    __syncthreads();
     const int inb = stage_in(stage), outb = stage_out(stage);
     const int txi = threadIdx.x % THREADS_X, tyi = threadIdx.x / THREADS_X;
+    const int wid = threadIdx.x >> 5;
 
     for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
         const int ii = find_inst(tprefix, ninst, tile);
@@ -444,8 +547,8 @@ stencil_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__restri
             const T *q0 = (const T *)d.q[0] + (long long)yt * pitch + xt;
             const QnSrc<T> qn{q0, q0 + plane, q0 + 2 * plane, pitch};
             const T src = d.s_amp != 0.0 ? (T)(d.s_amp * stage_sigma(d, stage)) : T(0);
-            tile_points<T, false, RY>(g0, g0 + plane, g0 + 2 * plane, pitch, qn, d, out, xt, yt, flags, stage, src,
-                                      txi, tyi, list, &list_n);
+            tile_points<T, RY, 0, true>(g0, g0 + plane, g0 + 2 * plane, pitch, qn, d, out, xt, yt,
+                                        stage_k<T>(d, stage), src, txi, tyi, wl.idx[wid], &wl.n[wid]);
             continue;
         }
 
@@ -479,10 +582,7 @@ stencil_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__restri
             *reinterpret_cast<Vec4<T> *>(su + r * BOX_X + c) = vu;
             *reinterpret_cast<Vec4<T> *>(sv + r * BOX_X + c) = vv;
         }
-        if (threadIdx.x == 0) {
-            s_src = d.s_amp != 0.0 ? (T)(d.s_amp * stage_sigma(d, stage)) : T(0);
-            list_n = 0;
-        }
+        if (threadIdx.x == 0) s_src = d.s_amp != 0.0 ? (T)(d.s_amp * stage_sigma(d, stage)) : T(0);
         __syncthreads();
         QnSrc<T> qn;
         if (stage == 1) {
@@ -491,13 +591,8 @@ stencil_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__restri
             const T *q0 = (const T *)d.q[0] + (long long)yt * pitch + xt;
             qn = QnSrc<T>{q0, q0 + plane, q0 + 2 * plane, pitch};
         }
-        tile_points<T, false, RY>(sp, su, sv, BOX_X, qn, d, out, xt, yt, flags, stage, s_src, txi, tyi, list,
-                                  &list_n);
-        if (flags & TILE_BAND) {
-            __syncthreads();
-            band_points<T>(sp, su, sv, BOX_X, qn, d, out, xt, yt, stage, list, min(list_n, LIST_CAP), threadIdx.x,
-                           STENCIL_THREADS);
-        }
+        tile_dispatch<T, RY, true>(flags, sp, su, sv, BOX_X, qn, d, out, xt, yt, stage_k<T>(d, stage), s_src, txi,
+                                   tyi, wl.idx[wid], &wl.n[wid]);
         __syncthreads();
     }
 }
@@ -521,6 +616,11 @@ template <int TW, int TH> struct TmaGeom {
     static_assert(BW <= 256 && BH <= 256, "TMA box dimensions are at most 256");
 };
 template <int TW, int TH, int RYT> __host__ __device__ constexpr int tma_threads() { return (TW / 4) * (TH / RYT); }
+// CTAs per SM the launch is sized for: two when two CTAs' stages fit in shared
+// memory and their threads in the register file at 128 registers each
+template <int TW, int TH, int RYT> __host__ __device__ constexpr int tma_ctas_per_sm() {
+    return (2 * TmaGeom<TW, TH>::SMEM + 8192 <= 227 * 1024 && tma_threads<TW, TH, RYT>() <= 256) ? 2 : 1;
+}
 constexpr int WAIT_SPINS = 1 << 20;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -553,7 +653,7 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const void *map, uint64_t
 }
 
 template <int TW, int TH, int RYT>
-__global__ void __launch_bounds__(tma_threads<TW, TH, RYT>(), 1)
+__global__ void __launch_bounds__(tma_threads<TW, TH, RYT>(), (tma_ctas_per_sm<TW, TH, RYT>()))
 stencil_tma_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ strips, int nstrips, int stage) {
     constexpr int NT = tma_threads<TW, TH, RYT>();
     using G = TmaGeom<TW, TH>;
@@ -561,12 +661,13 @@ stencil_tma_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ s
     constexpr uint32_t HALO_BYTES = G::BYTES;
     constexpr int BW = G::BW, BH = G::BH;
     extern __shared__ unsigned char smem_dyn[];
-    unsigned char *base = (unsigned char *)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
+    // 1024-byte aligned start, derived from the shared array so that the
+    // compiler keeps shared-memory (not generic) loads
+    unsigned char *base = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
     __shared__ __align__(8) uint64_t bar[TMA_STAGES];
     __shared__ int4 info[TMA_STAGES];  // (instance, x0, y0, flags) of the tile in each stage
     __shared__ float ssrc[TMA_STAGES]; // source amplitude x stage forcing of that tile's instance
-    __shared__ unsigned short list[LIST_CAP];
-    __shared__ int list_n[2];          // band-list counters, by tile parity
+    __shared__ WarpLists<NT / 32, RYT> wl;
     __shared__ int s_ntiles;
     __shared__ int abort_flag;
     const int tid = threadIdx.x;
@@ -592,10 +693,10 @@ stencil_tma_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ s
         s_ntiles = n;
         for (int b = 0; b < TMA_STAGES; ++b) mbar_init(&bar[b], 1);
         abort_flag = 0;
-        list_n[0] = list_n[1] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         for (int b = 0; b < TMA_STAGES - 1 && b < n; ++b) issue_next(b);
     }
+    wl.init();
     __syncthreads();
     const int ntiles = s_ntiles;
     const int txi = tid % (TW / 4), tyi = tid / (TW / 4);
@@ -605,9 +706,6 @@ stencil_tma_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ s
         // the stage freed at the end of tile k - 1 receives tile k + 2
         if (tid == 0 && k + TMA_STAGES - 1 < ntiles) issue_next((k + TMA_STAGES - 1) % TMA_STAGES);
         if (!mbar_wait_bounded(&bar[b], parity)) atomicExch(&abort_flag, 1);
-        // all threads are inside iteration k here: the counter of tile k + 1
-        // (last used by tile k - 1) can be cleared
-        if (tid == 0) list_n[(k & 1) ^ 1] = 0;
         const int4 inf = info[b];
         if (!abort_flag) {
             const InstDesc &d = inst[inf.x];
@@ -622,25 +720,147 @@ stencil_tma_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ s
                 qn = QnSrc<float>{q0, q0 + d.plane, q0 + 2 * d.plane, d.pitch};
             }
             float *out = (float *)d.q[outb];
-            tile_points<float, true, RYT>(sp, su, sv, BW, qn, d, out, inf.y, inf.z, (uint32_t)inf.w, stage,
-                                          ssrc[b], txi, tyi, list, &list_n[k & 1]);
-            if (inf.w & TILE_BAND) {
-                __syncthreads();
-                band_points<float>(sp, su, sv, BW, qn, d, out, inf.y, inf.z, stage, list, min(list_n[k & 1], LIST_CAP),
-                                   tid, NT);
-            }
+            tile_dispatch<float, RYT, true>((uint32_t)inf.w, sp, su, sv, BW, qn, d, out, inf.y, inf.z,
+                                            stage_k<float>(d, stage), ssrc[b], txi, tyi, wl.idx[tid >> 5],
+                                            &wl.n[tid >> 5]);
         }
         __syncthreads();                               // every thread is done with stage b
         if (abort_flag) {
             // a copy did not complete in time: flag the instance, let the copies
             // still in flight land, and leave
             if (tid == 0) {
-                atomicOr((unsigned long long *)&inst[inf.x].clock[2], 1ull);
+                atomicOr((unsigned long long *)&inst[inf.x].clock[2], STATUS_TIMEOUT);
                 for (int q = 1; q < TMA_STAGES && k + q < ntiles; ++q)
                     mbar_wait_bounded(&bar[(k + q) % TMA_STAGES], ((k + q) / TMA_STAGES) & 1);
             }
             return;
         }
+    }
+}
+
+// ---------------------------------------------------------------- TMA stencil, warp-specialised (FP32)
+// One producer warp and NC / 32 consumer warps per CTA, one CTA per SM.  For
+// each tile the producer's lane 0 copies, with TMA tensor loads into one of two
+// shared-memory stages, the (TW + 8) x (TH + 8) halo box of Q(k-1) and, from
+// stage 2 on, the TW x TH tile of Q^n; a "full" mbarrier per stage counts the
+// bytes.  Consumer warps compute the tile from shared memory only and each
+// arrives on the stage's "empty" mbarrier when it is done; the producer waits
+// for all of them before it refills the stage.  The tile loop has no block-
+// wide barrier, so warps drift up to one tile apart and the SM's issue slots
+// stay busy across tile boundaries.  Every wait is bounded: one that gives up
+// sets STATUS_TIMEOUT on the block's instances, the consumers stop, and the
+// producer lets each copy it issued land before the block exits.
+template <int TW, int TH, int RYT> struct WsGeom {
+    static constexpr int NC = (TW / 4) * (TH / RYT);           // consumer threads
+    static constexpr int NT = NC + 32;                         // + the producer warp
+    static constexpr int STAGES = 2;
+    static constexpr uint32_t HALO_BYTES = TmaGeom<TW, TH>::BYTES;
+    static constexpr uint32_t QN_BYTES = (uint32_t)TW * TH * 3 * 4;
+    static constexpr uint32_t STAGE_BYTES = HALO_BYTES + QN_BYTES;
+    static constexpr size_t SMEM = STAGES * (size_t)STAGE_BYTES + 1024;
+    static_assert(HALO_BYTES % 128 == 0 && STAGE_BYTES % 128 == 0, "stage layout keeps 128-byte alignment");
+    static_assert(SMEM + 1024 <= 227 * 1024, "two stages must fit in shared memory");
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// a bounded wait gave up: flag every instance this block works on
+__device__ __noinline__ void flag_block_timeout(const InstDesc *__restrict__ inst, const int4 *__restrict__ strips,
+                                                int nstrips) {
+    for (int s2 = blockIdx.x; s2 < nstrips; s2 += gridDim.x)
+        atomicOr((unsigned long long *)&inst[__ldg(strips + s2).x].clock[2], STATUS_TIMEOUT);
+}
+
+template <int TW, int TH, int RYT>
+__global__ void __launch_bounds__(WsGeom<TW, TH, RYT>::NT, 1)
+stencil_ws_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ strips, int nstrips, int stage) {
+    using W = WsGeom<TW, TH, RYT>;
+    constexpr int S = W::STAGES, NCW = W::NC / 32;
+    constexpr int BW = TmaGeom<TW, TH>::BW, BH = TmaGeom<TW, TH>::BH;
+    extern __shared__ unsigned char smem_dyn[];
+    unsigned char *base = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
+    __shared__ __align__(8) uint64_t full[S], empty[S];
+    __shared__ int4 info[S];           // (instance, x0, y0, flags) of the tile in each stage
+    __shared__ float ssrc[S];          // source amplitude x stage forcing of that tile's instance
+    __shared__ WarpLists<NCW, RYT> wl;
+    __shared__ int s_ntiles;
+    __shared__ volatile int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    wl.init();
+    const int inb = stage_in(stage), outb = stage_out(stage);
+    if (tid == 0) {
+        int n = 0;
+        for (int s2 = blockIdx.x; s2 < nstrips; s2 += gridDim.x) n += __ldg(strips + s2).w;
+        s_ntiles = n;
+        for (int b = 0; b < S; ++b) {
+            mbar_init(&full[b], 1);
+            mbar_init(&empty[b], NCW);
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int ntiles = s_ntiles;
+
+    if (warp == NCW) {
+        // ---- producer: lane 0 walks this block's strips (blockIdx.x + j * gridDim.x)
+        if (lane != 0) return;
+        int pj = 0, pr = 0, issued = 0;
+        for (int k = 0; k < ntiles; ++k) {
+            const int b = k % S;
+            // stage b last held tile k - S: wait until every consumer warp is done with it
+            if (k >= S && !mbar_wait_bounded(&empty[b], ((k / S) - 1) & 1)) {
+                abort_flag = 1;
+                flag_block_timeout(inst, strips, nstrips);
+            }
+            if (abort_flag) break;
+            const int4 st = __ldg(strips + blockIdx.x + pj * gridDim.x);
+            const InstDesc &d = inst[st.x];
+            const int ty = st.z + pr;
+            const int x0 = st.y * TW, y0 = ty * TH;
+            info[b] = make_int4(st.x, x0, y0, (int)__ldg(d.tile_flags + ty * d.tiles_x + st.y));
+            ssrc[b] = d.s_amp != 0.0 ? (float)(d.s_amp * stage_sigma(d, stage)) : 0.f;
+            unsigned char *sb = base + (size_t)b * W::STAGE_BYTES;
+            mbar_arrive_expect_tx(&full[b], stage == 1 ? W::HALO_BYTES : W::STAGE_BYTES);
+            tma_load_3d(sb, d.tmap[inb], &full[b], x0 - HALO, y0 - HALO, 0);
+            if (stage != 1) tma_load_3d(sb + W::HALO_BYTES, d.tmap[3], &full[b], x0, y0, 0);
+            ++issued;
+            if (++pr == st.w) { pr = 0; ++pj; }
+        }
+        if (abort_flag) {
+            // every copy issued must land before the block's shared memory goes away
+            for (int j = max(0, issued - S); j < issued; ++j) mbar_wait_bounded(&full[j % S], (j / S) & 1);
+        }
+        return;
+    }
+
+    // ---- consumers
+    const int txi = tid % (TW / 4), tyi = tid / (TW / 4);
+    for (int k = 0; k < ntiles; ++k) {
+        const int b = k % S;
+        if (!mbar_wait_bounded(&full[b], (k / S) & 1)) {
+            abort_flag = 1;
+            if (lane == 0) flag_block_timeout(inst, strips, nstrips);
+        }
+        if (abort_flag) break;
+        const int4 inf = info[b];
+        const InstDesc &d = inst[inf.x];
+        const float *sp = (const float *)(base + (size_t)b * W::STAGE_BYTES);
+        const float *su = sp + BW * BH;
+        const float *sv = su + BW * BH;
+        QnSrc<float> qn;
+        if (stage == 1) {
+            qn = QnSrc<float>{sp + HALO * BW + HALO, su + HALO * BW + HALO, sv + HALO * BW + HALO, BW};
+        } else {
+            const float *qs = sp + 3 * BW * BH;
+            qn = QnSrc<float>{qs, qs + TW * TH, qs + 2 * TW * TH, TW};
+        }
+        tile_dispatch<float, RYT, false>((uint32_t)inf.w, sp, su, sv, BW, qn, d, (float *)d.q[outb], inf.y, inf.z,
+                                         stage_k<float>(d, stage), ssrc[b], txi, tyi, wl.idx[warp], &wl.n[warp]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[b]);
     }
 }
 
@@ -655,6 +875,7 @@ __global__ void probe_kernel(const InstDesc *__restrict__ inst, const int *__res
         double s = 0.0;
         for (int e = 0; e < 16; ++e) s += d.p_w[16 * p + e] * (double)P[d.p_idx[16 * p + e]];
         d.p_hist[rec * d.np + p] = s;
+        if (!isfinite(s)) atomicOr((unsigned long long *)&d.clock[2], STATUS_DIVERGED);
     }
     __syncthreads();
     if (threadIdx.x == 0) d.clock[1] = rec + 1;
@@ -727,6 +948,12 @@ __global__ void energy_kernel(const InstDesc *__restrict__ dd) {
     if ((threadIdx.x & 31) == 0) atomicAdd(d.scratch, acc);
 }
 
+// status words of a batch's members, in member order
+__global__ void status_gather_kernel(const InstDesc *__restrict__ inst, int ninst, long long *out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ninst; i += gridDim.x * blockDim.x)
+        out[i] = inst[i].clock[2];
+}
+
 // ---------------------------------------------------------------- launchers
 namespace {
 template <typename T> size_t stencil_smem() { return (size_t)3 * SY * BOX_X * sizeof(T); }
@@ -765,6 +992,16 @@ int default_kernel_mode(int precision, bool periodic) {
     return KERNEL_TMA;
 }
 
+// warp-specialised TMA kernel with 64 x 60 tiles (LEE_TMA_WS=0: the 3-stage
+// kernel whose threads read Q^n from global memory, 64 x 64 tiles)
+bool tma_ws() {
+    static int w = [] {
+        const char *e = getenv("LEE_TMA_WS");
+        return e ? atoi(e) : 1;
+    }();
+    return w != 0;
+}
+
 // rows per thread of the TMA kernel (4: 256 threads, 2: 512 threads)
 int tma_rows() {
     static int r = [] {
@@ -787,6 +1024,10 @@ cudaError_t prepare_kernels(int precision) {
             cudaError_t e = tma_attr<64, 64, 2>();
             if (e == cudaSuccess) e = tma_attr<64, 64, 4>();
             if (e == cudaSuccess) e = tma_attr<128, 32, 2>();
+            if (e == cudaSuccess) e = tma_attr<64, 32, 2>();
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(stencil_ws_kernel<64, 60, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)WsGeom<64, 60, 2>::SMEM);
             if (e != cudaSuccess) return e;
             done = true;
         }
@@ -797,13 +1038,17 @@ cudaError_t prepare_kernels(int precision) {
     return setup_stencil_attr<double>();
 }
 
-// TMA tile width of FP32 instances: LEE_TMA_TILE = 64x64 (default) or 128x32
+// TMA tile of FP32 instances: 64 x 60 for the warp-specialised kernel
+// (default), else LEE_TMA_TILE = 64x64, 64x32 or 128x32
 void tma_tile(int &tw, int &th) {
     static int w = 0, h = 0;
     if (!w) {
         const char *e = getenv("LEE_TMA_TILE");
-        const std::string v = e ? e : "64x64";
-        if (v == "128x32") { w = 128; h = 32; } else { w = 64; h = 64; }
+        const std::string v = e ? e : (tma_ws() ? "64x60" : "64x64");
+        if (v == "128x32") { w = 128; h = 32; }
+        else if (v == "64x32") { w = 64; h = 32; }
+        else if (v == "64x60") { w = 64; h = 60; }
+        else { w = 64; h = 64; }
     }
     tw = w; th = h;
 }
@@ -862,8 +1107,21 @@ cudaError_t launch_stencil(const BatchView &bv, int stage, int persistent_ctas, 
     cudaError_t e;
     if (bv.precision == 1 && bv.kernel_mode == KERNEL_TMA) {
         if (bv.total_tiles == 0) return cudaSuccess;
-        const int grid = std::min(bv.nstrips, persistent_ctas > 0 ? persistent_ctas : num_sms());
-        if (bv.tile_w == 128)
+        auto grid_for = [&](int per_sm) {
+            return std::min(bv.nstrips, persistent_ctas > 0 ? persistent_ctas : per_sm * num_sms());
+        };
+        if (bv.tile_w == 64 && bv.tile_h == 32) {
+            constexpr int C = tma_ctas_per_sm<64, 32, 2>();
+            stencil_tma_kernel<64, 32, 2><<<grid_for(C), tma_threads<64, 32, 2>(), TmaGeom<64, 32>::SMEM, s>>>(
+                bv.inst, bv.strips, bv.nstrips, stage);
+            count_launch();
+            return cudaGetLastError();
+        }
+        const int grid = grid_for(1);
+        if (bv.tile_w == 64 && bv.tile_h == 60)
+            stencil_ws_kernel<64, 60, 2><<<grid, WsGeom<64, 60, 2>::NT, WsGeom<64, 60, 2>::SMEM, s>>>(
+                bv.inst, bv.strips, bv.nstrips, stage);
+        else if (bv.tile_w == 128)
             stencil_tma_kernel<128, 32, 2><<<grid, tma_threads<128, 32, 2>(), TmaGeom<128, 32>::SMEM, s>>>(
                 bv.inst, bv.strips, bv.nstrips, stage);
         else if (tma_rows() == 4)
@@ -941,6 +1199,13 @@ cudaError_t launch_energy(const InstDesc *dinst, const InstDesc &h, cudaStream_t
     const int blocks = (int)std::min<long long>((n + 255) / 256, kGridStrideBlocks);
     if (h.precision == 1) energy_kernel<float><<<blocks, 256, 0, s>>>(dinst);
     else energy_kernel<double><<<blocks, 256, 0, s>>>(dinst);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_status_gather(const BatchView &bv, long long *out, cudaStream_t s) {
+    if (bv.ninst <= 0) return cudaSuccess;
+    status_gather_kernel<<<(bv.ninst + 255) / 256, 256, 0, s>>>(bv.inst, bv.ninst, out);
     count_launch();
     return cudaGetLastError();
 }

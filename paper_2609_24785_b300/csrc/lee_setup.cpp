@@ -184,6 +184,20 @@ std::complex<double> rk4_poly(std::complex<double> z) {
 
 }  // namespace
 
+void fill_stage_constants(double dt, double h, float kf[4][8], double kd[4][8]) {
+    static const double alpha[4] = {0.25, 1.0 / 3.0, 0.5, 1.0};       // 2N-storage Jameson scheme
+    static const double a[3] = {0.770882380518, -0.166705904415, 0.020843142770};  // DRP, Sec. 2.2
+    const double inv_h = 1.0 / h;
+    for (int k = 0; k < 4; ++k) {
+        const double ad = alpha[k] * dt, adh = ad * inv_h;
+        double v[8] = {ad, adh * a[0], adh * a[1], adh * a[2], adh * SPONGE_K, inv_h, SPONGE_K * inv_h, 0.0};
+        for (int i = 0; i < 8; ++i) {
+            kd[k][i] = v[i];
+            kf[k][i] = (float)v[i];
+        }
+    }
+}
+
 void stage_forcing_factors(double omega, double dt, double G_re[4], double G_im[4]) {
     // Stage k uses the moment of order j = 4 - k of sin(w t) over the step:
     // (j+1)!/dt^(j+1) int_0^dt (dt - s)^j / j! e^{i w s} ds
@@ -245,7 +259,7 @@ int build_plan(int nx, int ny, double h, double x0, double y0, int per_x, int pe
     if (ng > 0 && geo.kind == 0) { err = "ghost points without a wall"; return LEE_ERR_GEOMETRY; }
 
     // ---- per-ghost reconstruction
-    struct GOut { int m; std::vector<int> idx; std::vector<double> w; double kp, ku, meta[5]; int status; };
+    struct GOut { int m, k; std::vector<int> idx; std::vector<double> w; double kp, ku, meta[5]; int status; };
     std::vector<GOut> out(ng);
 #pragma omp parallel for schedule(dynamic, 8)
     for (int g = 0; g < ng; ++g) {
@@ -292,7 +306,15 @@ int build_plan(int nx, int ny, double h, double x0, double y0, int per_x, int pe
         std::vector<xr> L((size_t)(KMAX + 1) * (N > 0 ? N : 1));
         int m = KMAX;
         while (m >= 1 && !readout_rows(N, xp, yp, m, L.data())) --m;
-        if (m < 1) { G.status = LEE_ERR_RANK; continue; }
+        G.k = m >= 1 ? m : 0;
+        if (m < 1) {
+            // no plane through the cloud (its nodes on one line, where a steep
+            // wall leaves the box): constant fit = cloud mean, read out at
+            // P_0 and P_1, with a linear extrapolation along the normal
+            if (N < 1) { G.status = LEE_ERR_RANK; continue; }
+            for (int e = 0; e < N; ++e) L[e] = L[(size_t)N + e] = 1.0L / (xr)N;
+            m = 1;
+        }
         G.m = m;
         xr dir[KMAX + 1], neu[KMAX + 1], kd, kn;
         normal_factors(m, r, dir, kd, neu, kn);
@@ -319,14 +341,14 @@ int build_plan(int nx, int ny, double h, double x0, double y0, int per_x, int pe
         if (out[g].status) {
             char b[160];
             snprintf(b, sizeof b, "ghost %d at node %d: %s", g, P.g_target[g],
-                     out[g].status == LEE_ERR_RANK ? "cloud rank deficient at degree 1" : "cloud too large");
+                     out[g].status == LEE_ERR_RANK ? "cloud holds no fluid node" : "cloud too large");
             err = b;
             return out[g].status;
         }
         P.g_start[g + 1] = P.g_start[g] + (int)out[g].idx.size();
         for (int q = 0; q < 5; ++q) P.g_meta[(size_t)5 * g + q] = out[g].meta[q];
         P.g_m[g] = out[g].m;
-        P.n_reduced += out[g].m < KMAX;
+        P.n_reduced += out[g].k < KMAX;
         P.g_kappa[2 * g] = out[g].kp;
         P.g_kappa[2 * g + 1] = out[g].ku;
     }

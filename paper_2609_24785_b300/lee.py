@@ -21,6 +21,7 @@ LEE_OK, LEE_ERR_ARG, LEE_ERR_GEOMETRY, LEE_ERR_RANK, LEE_ERR_ADE_UNSTABLE, LEE_E
 LEE_FP64, LEE_FP32 = 0, 1
 LEE_BC_RADIATION, LEE_BC_PERIODIC = 0, 1
 LEE_P, LEE_U, LEE_V = 0, 1, 2
+STATUS_TIMEOUT, STATUS_DIVERGED = 1, 2      # bits of a member's status word (Batch.status)
 _STATUS = {1: "ARG", 2: "GEOMETRY", 3: "RANK", 4: "ADE_UNSTABLE", 5: "BUDGET", 6: "CUDA", 7: "DIVERGED", 8: "TIMEOUT"}
 
 
@@ -88,6 +89,7 @@ SIGNATURES = {
     "lee_batch_step": (C.c_int, [_vp, C.c_longlong]),
     "lee_batch_last_error": (C.c_char_p, [_vp]),
     "lee_batch_launch": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "lee_batch_status": (C.c_int, [_vp, _llp, C.c_int]),
     "lee_energy_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, C.c_int, C.c_longlong, C.c_int, C.c_double,
                                       _vp, _vp]),
     "lee_launch_count": (C.c_longlong, []),
@@ -328,6 +330,14 @@ class Batch:
 
     def sync(self):
         self.stream.synchronize()
+
+    def status(self):
+        """Members' status words after the batch stream drains (0 healthy,
+        STATUS_TIMEOUT, STATUS_DIVERGED bits), in member order."""
+        n = len(self.members)
+        out = np.zeros(max(n, 1), dtype=np.int64)
+        self._c(self.L.lee_batch_status(self.b, out.ctypes.data_as(_llp), n))
+        return out[:n]
 
     def launch(self, stage, what):
         """Measurement hook: one ghost (what=0) or stencil (what=1) launch of a stage."""

@@ -64,6 +64,11 @@ def _compare_plan(case):
     workloads.cylinder_pulse(256),
     workloads.cylinder_pulse(300, nx=300, ny=220),
     workloads.monopole(256, radius_cells=13.3, src_cells=40),
+    # steep wall leaving the box: clouds on one line take the constant fit
+    workloads.Case("steep_line", 48, 48, wall=("line", 23.87 * 0.01, 23.5 * 0.01, math.radians(35.0)),
+                   imp=("msd", 1.0, 0.05, 5.0)),
+    workloads.Case("steep_line_768", 768, 768, wall=("line", 3.8387, 3.835, 0.8203129105709946),
+                   imp=("msd", 1.0, 0.05, 5.0)),
 ], ids=lambda c: c.name)
 def test_plan_matches_oracle(case):
     worst, s, o = _compare_plan(case)

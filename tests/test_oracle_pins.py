@@ -210,7 +210,7 @@ def _reproduce(o, deg, seed=0):
     scale = max(np.abs(f(Xr, Yr)).max() for f in (fp, fu, fv))
     err = []
     for g, G in enumerate(gh):
-        if G["m"] < min(deg, 4):
+        if G["k"] < min(deg, 4):
             continue
         t = G["target"]
         xg, yg = Xr.reshape(-1)[t], Yr.reshape(-1)[t]
@@ -235,6 +235,32 @@ def test_ghost_fill_reproduces_degree4_polynomials(geom):
         assert max(e for e, _ in err) < 1e-9, (deg, max(err))
     err5 = _reproduce(o, 5, seed=7)
     assert max(e for e, m in err5 if m == 4) > 1e-7
+
+
+def test_constant_fit_fallback_where_a_cloud_lies_on_one_line():
+    """A steep wall leaving the box can clip a cloud to nodes on one line, which
+    carries no plane: that ghost takes the constant fit (read-out rows 1/N at
+    P_0 and P_1, linear normal extrapolation).  Such ghosts reproduce constant
+    fields exactly; every other ghost still reproduces polynomials up to its
+    fit degree."""
+    o = _line(48, 35).setup()
+    gh = [o.ghost(g) for g in range(o.n_ghost)]
+    k0 = [G for G in gh if G["k"] == 0]
+    assert k0, "geometry no longer exercises the fallback"
+    for G in k0:
+        N = len(G["cloud"])
+        assert G["m"] == 1 and G["L"].shape == (2, N)
+        np.testing.assert_array_equal(G["L"], np.full((2, N), 1.0 / N))
+        # the cloud is collinear: rank 1 after removing its mean point
+        cl = G["cloud"]
+        pts = np.stack([cl % o.nx, cl // o.nx], 1).astype(float)
+        assert np.linalg.matrix_rank(pts - pts.mean(0), tol=1e-9) <= 1
+    assert o.n_reduced >= len(k0)
+    for deg in (0, 1, 2, 4):
+        err = _reproduce(o, deg, seed=11 + deg)
+        if deg == 0:
+            assert len(err) == o.n_ghost             # every ghost, the constant-fit ones included
+        assert max(e for e, _ in err) < 1e-9, (deg, max(err))
 
 
 @pytest.mark.parametrize("geom", ["cyl", 30])
