@@ -69,21 +69,6 @@ def peaks():
     return 6400.0, "fallback"
 
 
-def stencil_kernel_name(precision):
-    """The stencil kernel the library picks for non-periodic instances (its
-    LEE_FP32_KERNEL / LEE_FP64_KERNEL / LEE_TMA_TILE / LEE_TMA_RY selection)."""
-    if precision == "fp32":
-        mode = os.environ.get("LEE_FP32_KERNEL", "tma")
-        if mode == "tma":
-            tile = os.environ.get("LEE_TMA_TILE", "64x64")
-            ry = 4 if os.environ.get("LEE_TMA_RY") == "4" and tile == "64x64" else 2
-            w, h = tile.split("x") if tile in ("64x32", "128x32") else ("64", "64")
-            return "stencil_tma_kernel<%s,%s,%d>" % (w, h, ry)
-        return "stencil_kernel<float,%s>" % ("true" if mode == "direct" else "false")
-    mode = os.environ.get("LEE_FP64_KERNEL", "smem")
-    return "stencil_kernel<double,%s>" % ("true" if mode == "direct" else "false")
-
-
 def workload_cases(args, rank, accept=None):
     from paper_2609_24785_b300 import workloads
     if args.workload == "sweep":
@@ -404,7 +389,7 @@ def run_lee(args):
                        "parallelism": "replicas" if ws > 1 else "single GPU", "setup_s": round(t_setup, 2)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": stencil_kernel_name(args.precision) + " stage 2",
+                         "kernel": batch.stencil_kernel() + " stage 2",
                          "launch_ms": st_ms, "alg_bytes_per_launch": int(alg_bytes),
                          "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind},
             "ghost_kernel_ms": gh_ms,

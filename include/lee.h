@@ -216,6 +216,9 @@ const char *lee_batch_last_error(const lee_batch *b);
  * bit 1 = a ghost, ADE or probe value became non-finite (diverged).  One small
  * gather kernel and one copy; LEE_ERR_ARG if n differs from the member count. */
 int lee_batch_status(lee_batch *b, long long *host, int n);
+/* Name of the stencil kernel variant the batch launches (static string; ""
+ * before lee_batch_bind or without members). */
+const char *lee_batch_stencil_kernel(lee_batch *b);
 /* Measurement hook: enqueue only one kernel of stage `stage` (1..4) for every
  * member: what = 0 ghost/ADE kernel, 1 stencil kernel.  Stages 2..4 read and
  * write disjoint buffers, so repeated launches are idempotent. */

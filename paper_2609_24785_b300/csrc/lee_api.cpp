@@ -863,6 +863,12 @@ int lee_batch_status(lee_batch *b, long long *host, int n) {
     return LEE_OK;
 }
 
+const char *lee_batch_stencil_kernel(lee_batch *b) {
+    if (!b || !b->dev) return "";
+    if (b->dirty && batch_refresh(b) != LEE_OK) return "";
+    return b->members.empty() ? "" : stencil_kernel_name(b->bv);
+}
+
 int lee_batch_launch(lee_batch *b, int stage, int what) {
     if (!b || stage < 1 || stage > 4 || what < 0 || what > 1) return LEE_ERR_ARG;
     if (!b->dev) { b->err = "batch not bound"; return LEE_ERR_ARG; }

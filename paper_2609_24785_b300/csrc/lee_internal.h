@@ -15,7 +15,7 @@ namespace lee {
 constexpr int TILE_X = 64;
 constexpr int TILE_Y = 32;
 constexpr int TMA_TILE_Y = 64;
-constexpr int GHOST_LANES = 8;          // lanes per ghost point in the ghost kernel
+constexpr int GHOST_LANES = 4;          // lanes per ghost point in the ghost kernel
 // stencil kernel variants
 constexpr int KERNEL_SMEM = 0;          // threads stage the halo box in shared memory (64 x 32 tiles)
 constexpr int KERNEL_DIRECT = 1;        // interior tiles read global memory directly (64 x 32 tiles)
@@ -52,8 +52,9 @@ void fill_stage_constants(double dt, double h, float kf[4][8], double kd[4][8]);
 // Neumann row wp, Dirichlet row wd, free-extrapolation row wf.
 struct alignas(32) GW { double l0, wp, wd, wf; };
 
-// Per-instance descriptor read by every kernel (device copy in the arena).
-struct InstDesc {
+// Per-instance descriptor read by every kernel (device copy in the arena;
+// copied whole into shared memory in 16-byte pieces by the TMA kernel).
+struct alignas(16) InstDesc {
     void *q[3];                 // buffers Q^n, Q^a, Q^b; each holds planes p,u,v
     long long plane;            // elements per plane = ny * pitch
     const uint8_t *mask;        // node kind, ny x pitch (0 solid, 1 fluid, 2 ghost)
@@ -94,6 +95,7 @@ struct InstDesc {
     double *staging;            // nx * ny doubles for host transfers
     int precision;
 };
+static_assert(sizeof(InstDesc) % 16 == 0, "InstDesc is copied in 16-byte pieces");
 
 // Host-side plan of one instance.
 struct Plan {
@@ -168,6 +170,7 @@ cudaError_t launch_to_staging(const InstDesc *dinst, const InstDesc &h, int whic
 cudaError_t launch_from_staging(const InstDesc *dinst, const InstDesc &h, int which, cudaStream_t s);
 cudaError_t launch_energy(const InstDesc *dinst, const InstDesc &h, cudaStream_t s);
 cudaError_t launch_status_gather(const BatchView &bv, long long *out, cudaStream_t s);
+const char *stencil_kernel_name(const BatchView &bv);
 long long launch_count();
 void count_launch(int n = 1);
 // message for lee_last_error(NULL) (entry points without a context)

@@ -59,9 +59,33 @@ __device__ __forceinline__ GW ldg_gw(const GW *p) {
 }
 
 // ---------------------------------------------------------------- ghosts
+// FP32 -> FP64 widening on the integer pipe, exact for every input (the
+// hardware conversion shares the FP64 pipe with the gather's FMAs): the sign
+// moves up, the exponent is rebiased, subnormals are normalised first, the
+// mantissa is shifted into place; zeros, infinities and NaNs keep their class.
+__device__ __forceinline__ double widen_f32(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+    const unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    unsigned long long bits;
+    if (e == 0xffu) {
+        bits = 0x7ff0000000000000ull | ((unsigned long long)m << 29);
+    } else if (e != 0) {
+        bits = ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+    } else if (m == 0) {
+        bits = 0;
+    } else {                                        // m 2^-149 = (1 + f) 2^(p - 149)
+        const int p = 31 - __clz(m);
+        bits = ((unsigned long long)(p + 874) << 52) | (((unsigned long long)m << (52 - p)) & 0xfffffffffffffull);
+    }
+    return __longlong_as_double((long long)(sign | bits));
+}
+template <bool INTW> __device__ __forceinline__ double to_f64(float x) { return INTW ? widen_f32(x) : (double)x; }
+template <bool INTW> __device__ __forceinline__ double to_f64(double x) { return x; }
+
 // One CTA handles GHOSTS_PER_CTA ghosts of one instance (a chunk of the work
 // list), GHOST_LANES lanes per ghost point.
-template <typename T>
+template <typename T, bool INTW>
 __global__ void __launch_bounds__(GHOST_THREADS)
 ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int4 *__restrict__ chunks, int nchunks,
              int stage) {
@@ -102,17 +126,17 @@ ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int4 *__restric
     for (; e + GHOST_LANES < e1; e += 2 * GHOST_LANES) {
         const int ia = __ldg(d.e_idx + e), ib = __ldg(d.e_idx + e + GHOST_LANES);
         const GW wa = ldg_gw(d.e_w + e), wb = ldg_gw(d.e_w + e + GHOST_LANES);
-        const double pa = (double)P[ia], ua = (double)U[ia], va = (double)V[ia];
-        const double pb = (double)P[ib], ub = (double)U[ib], vb = (double)V[ib];
+        const double pa = to_f64<INTW>(P[ia]), ua = to_f64<INTW>(U[ia]), va = to_f64<INTW>(V[ia]);
+        const double pb = to_f64<INTW>(P[ib]), ub = to_f64<INTW>(U[ib]), vb = to_f64<INTW>(V[ib]);
         accumulate(wa, pa, ua, va);
         accumulate(wb, pb, ub, vb);
     }
     if (e < e1) {
         const int ia = __ldg(d.e_idx + e);
         const GW wa = ldg_gw(d.e_w + e);
-        accumulate(wa, (double)P[ia], (double)U[ia], (double)V[ia]);
+        accumulate(wa, to_f64<INTW>(P[ia]), to_f64<INTW>(U[ia]), to_f64<INTW>(V[ia]));
     }
-    const unsigned gmask = 0xffu << (threadIdx.x & 24);
+    const unsigned gmask = ((1u << GHOST_LANES) - 1u) << (threadIdx.x & (32 - GHOST_LANES));
 #pragma unroll
     for (int o = GHOST_LANES / 2; o > 0; o >>= 1) {
         s0 += __shfl_xor_sync(gmask, s0, o, GHOST_LANES);
@@ -750,16 +774,21 @@ stencil_tma_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ s
 // stay busy across tile boundaries.  Every wait is bounded: one that gives up
 // sets STATUS_TIMEOUT on the block's instances, the consumers stop, and the
 // producer lets each copy it issued land before the block exits.
-template <int TW, int TH, int RYT> struct WsGeom {
+template <int TW, int TH, int RYT, int S_> struct WsGeom {
     static constexpr int NC = (TW / 4) * (TH / RYT);           // consumer threads
     static constexpr int NT = NC + 32;                         // + the producer warp
-    static constexpr int STAGES = 2;
+    static constexpr int STAGES = S_;
     static constexpr uint32_t HALO_BYTES = TmaGeom<TW, TH>::BYTES;
     static constexpr uint32_t QN_BYTES = (uint32_t)TW * TH * 3 * 4;
     static constexpr uint32_t STAGE_BYTES = HALO_BYTES + QN_BYTES;
     static constexpr size_t SMEM = STAGES * (size_t)STAGE_BYTES + 1024;
+    // static shared memory: band lists, descriptors, barriers
+    static constexpr size_t STATIC = (NC / 32) * (128 * RYT * 2 + 4) + STAGES * (sizeof(InstDesc) + 40) + 320;
+    // two CTAs per SM when both fit in shared memory and the register file
+    static constexpr int CTAS = (2 * (SMEM + STATIC + 1024) <= 228 * 1024 && 2 * NT * 128 <= 65536) ? 2 : 1;
+    static_assert(NC % 32 == 0, "whole consumer warps");
     static_assert(HALO_BYTES % 128 == 0 && STAGE_BYTES % 128 == 0, "stage layout keeps 128-byte alignment");
-    static_assert(SMEM + 1024 <= 227 * 1024, "two stages must fit in shared memory");
+    static_assert(SMEM + STATIC <= 227 * 1024, "the stages must fit in shared memory");
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
@@ -773,10 +802,10 @@ __device__ __noinline__ void flag_block_timeout(const InstDesc *__restrict__ ins
         atomicOr((unsigned long long *)&inst[__ldg(strips + s2).x].clock[2], STATUS_TIMEOUT);
 }
 
-template <int TW, int TH, int RYT>
-__global__ void __launch_bounds__(WsGeom<TW, TH, RYT>::NT, 1)
+template <int TW, int TH, int RYT, int S_>
+__global__ void __launch_bounds__(WsGeom<TW, TH, RYT, S_>::NT, WsGeom<TW, TH, RYT, S_>::CTAS)
 stencil_ws_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ strips, int nstrips, int stage) {
-    using W = WsGeom<TW, TH, RYT>;
+    using W = WsGeom<TW, TH, RYT, S_>;
     constexpr int S = W::STAGES, NCW = W::NC / 32;
     constexpr int BW = TmaGeom<TW, TH>::BW, BH = TmaGeom<TW, TH>::BH;
     extern __shared__ unsigned char smem_dyn[];
@@ -784,6 +813,7 @@ stencil_ws_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ st
     __shared__ __align__(8) uint64_t full[S], empty[S];
     __shared__ int4 info[S];           // (instance, x0, y0, flags) of the tile in each stage
     __shared__ float ssrc[S];          // source amplitude x stage forcing of that tile's instance
+    __shared__ __align__(16) InstDesc sdesc[S];   // the tile's instance descriptor
     __shared__ WarpLists<NCW, RYT> wl;
     __shared__ int s_ntiles;
     __shared__ volatile int abort_flag;
@@ -805,31 +835,43 @@ stencil_ws_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ st
     const int ntiles = s_ntiles;
 
     if (warp == NCW) {
-        // ---- producer: lane 0 walks this block's strips (blockIdx.x + j * gridDim.x)
-        if (lane != 0) return;
+        // ---- producer warp: walks this block's strips (blockIdx.x + j * gridDim.x).
+        // Lane 0 waits for the stage and issues the copies; the whole warp
+        // copies the tile's instance descriptor into the stage's shared slot,
+        // so that consumers read every parameter from shared memory.
         int pj = 0, pr = 0, issued = 0;
         for (int k = 0; k < ntiles; ++k) {
             const int b = k % S;
             // stage b last held tile k - S: wait until every consumer warp is done with it
-            if (k >= S && !mbar_wait_bounded(&empty[b], ((k / S) - 1) & 1)) {
+            int ok = 1;
+            if (lane == 0 && k >= S && !mbar_wait_bounded(&empty[b], ((k / S) - 1) & 1)) {
                 abort_flag = 1;
                 flag_block_timeout(inst, strips, nstrips);
             }
-            if (abort_flag) break;
+            if (lane == 0) ok = !abort_flag;
+            if (!__shfl_sync(0xffffffffu, ok, 0)) break;
             const int4 st = __ldg(strips + blockIdx.x + pj * gridDim.x);
-            const InstDesc &d = inst[st.x];
             const int ty = st.z + pr;
-            const int x0 = st.y * TW, y0 = ty * TH;
-            info[b] = make_int4(st.x, x0, y0, (int)__ldg(d.tile_flags + ty * d.tiles_x + st.y));
-            ssrc[b] = d.s_amp != 0.0 ? (float)(d.s_amp * stage_sigma(d, stage)) : 0.f;
-            unsigned char *sb = base + (size_t)b * W::STAGE_BYTES;
-            mbar_arrive_expect_tx(&full[b], stage == 1 ? W::HALO_BYTES : W::STAGE_BYTES);
-            tma_load_3d(sb, d.tmap[inb], &full[b], x0 - HALO, y0 - HALO, 0);
-            if (stage != 1) tma_load_3d(sb + W::HALO_BYTES, d.tmap[3], &full[b], x0, y0, 0);
+            {
+                const int4 *src4 = reinterpret_cast<const int4 *>(inst + st.x);
+                int4 *dst4 = reinterpret_cast<int4 *>(&sdesc[b]);
+                for (int i = lane; i < (int)(sizeof(InstDesc) / 16); i += 32) dst4[i] = __ldg(src4 + i);
+            }
+            __syncwarp();
+            if (lane == 0) {
+                const InstDesc &d = sdesc[b];
+                const int x0 = st.y * TW, y0 = ty * TH;
+                info[b] = make_int4(st.x, x0, y0, (int)__ldg(d.tile_flags + ty * d.tiles_x + st.y));
+                ssrc[b] = d.s_amp != 0.0 ? (float)(d.s_amp * stage_sigma(d, stage)) : 0.f;
+                unsigned char *sb = base + (size_t)b * W::STAGE_BYTES;
+                mbar_arrive_expect_tx(&full[b], stage == 1 ? W::HALO_BYTES : W::STAGE_BYTES);
+                tma_load_3d(sb, d.tmap[inb], &full[b], x0 - HALO, y0 - HALO, 0);
+                if (stage != 1) tma_load_3d(sb + W::HALO_BYTES, d.tmap[3], &full[b], x0, y0, 0);
+            }
             ++issued;
             if (++pr == st.w) { pr = 0; ++pj; }
         }
-        if (abort_flag) {
+        if (lane == 0 && abort_flag) {
             // every copy issued must land before the block's shared memory goes away
             for (int j = max(0, issued - S); j < issued; ++j) mbar_wait_bounded(&full[j % S], (j / S) & 1);
         }
@@ -846,7 +888,7 @@ stencil_ws_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ st
         }
         if (abort_flag) break;
         const int4 inf = info[b];
-        const InstDesc &d = inst[inf.x];
+        const InstDesc &d = sdesc[b];
         const float *sp = (const float *)(base + (size_t)b * W::STAGE_BYTES);
         const float *su = sp + BW * BH;
         const float *sv = su + BW * BH;
@@ -992,8 +1034,8 @@ int default_kernel_mode(int precision, bool periodic) {
     return KERNEL_TMA;
 }
 
-// warp-specialised TMA kernel with 64 x 60 tiles (LEE_TMA_WS=0: the 3-stage
-// kernel whose threads read Q^n from global memory, 64 x 64 tiles)
+// warp-specialised TMA kernel (LEE_TMA_WS=0: the 3-stage kernel whose
+// threads read Q^n from global memory)
 bool tma_ws() {
     static int w = [] {
         const char *e = getenv("LEE_TMA_WS");
@@ -1017,6 +1059,18 @@ template <int TW, int TH, int RYT> cudaError_t tma_attr() {
                                 (int)TmaGeom<TW, TH>::SMEM);
 }
 
+template <int TW, int TH, int RYT, int S_> cudaError_t ws_attr() {
+    return cudaFuncSetAttribute(stencil_ws_kernel<TW, TH, RYT, S_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)WsGeom<TW, TH, RYT, S_>::SMEM);
+}
+
+template <int TW, int TH, int RYT, int S_>
+void launch_ws(const BatchView &bv, int stage, int persistent_ctas, cudaStream_t s) {
+    using W = WsGeom<TW, TH, RYT, S_>;
+    const int grid = std::min(bv.nstrips, persistent_ctas > 0 ? persistent_ctas : W::CTAS * num_sms());
+    stencil_ws_kernel<TW, TH, RYT, S_><<<grid, W::NT, W::SMEM, s>>>(bv.inst, bv.strips, bv.nstrips, stage);
+}
+
 cudaError_t prepare_kernels(int precision) {
     if (precision == 1) {
         static bool done = false;
@@ -1025,9 +1079,11 @@ cudaError_t prepare_kernels(int precision) {
             if (e == cudaSuccess) e = tma_attr<64, 64, 4>();
             if (e == cudaSuccess) e = tma_attr<128, 32, 2>();
             if (e == cudaSuccess) e = tma_attr<64, 32, 2>();
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(stencil_ws_kernel<64, 60, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)WsGeom<64, 60, 2>::SMEM);
+            if (e == cudaSuccess) e = ws_attr<64, 60, 2, 2>();
+            if (e == cudaSuccess) e = ws_attr<64, 40, 2, 3>();
+            if (e == cudaSuccess) e = ws_attr<64, 32, 2, 3>();
+            if (e == cudaSuccess) e = ws_attr<64, 24, 2, 2>();
+            if (e == cudaSuccess) e = ws_attr<128, 28, 2, 2>();
             if (e != cudaSuccess) return e;
             done = true;
         }
@@ -1038,16 +1094,20 @@ cudaError_t prepare_kernels(int precision) {
     return setup_stencil_attr<double>();
 }
 
-// TMA tile of FP32 instances: 64 x 60 for the warp-specialised kernel
-// (default), else LEE_TMA_TILE = 64x64, 64x32 or 128x32
+// TMA tile of FP32 instances, LEE_TMA_TILE: warp-specialised kernel 128x28
+// (default: 512-byte rows), 64x60, 64x40, 64x32 or 64x24; LEE_TMA_WS=0:
+// 64x64, 64x32 or 128x32
 void tma_tile(int &tw, int &th) {
     static int w = 0, h = 0;
     if (!w) {
         const char *e = getenv("LEE_TMA_TILE");
-        const std::string v = e ? e : (tma_ws() ? "64x60" : "64x64");
+        const std::string v = e ? e : (tma_ws() ? "128x28" : "64x64");
         if (v == "128x32") { w = 128; h = 32; }
         else if (v == "64x32") { w = 64; h = 32; }
         else if (v == "64x60") { w = 64; h = 60; }
+        else if (v == "64x40") { w = 64; h = 40; }
+        else if (v == "64x24") { w = 64; h = 24; }
+        else if (v == "128x28") { w = 128; h = 28; }
         else { w = 64; h = 64; }
     }
     tw = w; th = h;
@@ -1095,10 +1155,16 @@ bool encode_tensor_maps(const InstDesc &d, void *host_out, std::string &err) {
 
 cudaError_t launch_ghost(const BatchView &bv, int stage, cudaStream_t s) {
     const int blocks = bv.nchunks > 0 ? bv.nchunks : 1;
-    if (bv.precision == 1)
-        ghost_kernel<float><<<blocks, GHOST_THREADS, 0, s>>>(bv.inst, bv.ninst, bv.ghost_chunks, bv.nchunks, stage);
+    static const bool intw = [] {
+        const char *e = getenv("LEE_GHOST_WIDEN");
+        return !(e && std::string(e) == "hw");
+    }();
+    if (bv.precision == 1 && intw)
+        ghost_kernel<float, true><<<blocks, GHOST_THREADS, 0, s>>>(bv.inst, bv.ninst, bv.ghost_chunks, bv.nchunks, stage);
+    else if (bv.precision == 1)
+        ghost_kernel<float, false><<<blocks, GHOST_THREADS, 0, s>>>(bv.inst, bv.ninst, bv.ghost_chunks, bv.nchunks, stage);
     else
-        ghost_kernel<double><<<blocks, GHOST_THREADS, 0, s>>>(bv.inst, bv.ninst, bv.ghost_chunks, bv.nchunks, stage);
+        ghost_kernel<double, false><<<blocks, GHOST_THREADS, 0, s>>>(bv.inst, bv.ninst, bv.ghost_chunks, bv.nchunks, stage);
     count_launch();
     return cudaGetLastError();
 }
@@ -1110,7 +1176,7 @@ cudaError_t launch_stencil(const BatchView &bv, int stage, int persistent_ctas, 
         auto grid_for = [&](int per_sm) {
             return std::min(bv.nstrips, persistent_ctas > 0 ? persistent_ctas : per_sm * num_sms());
         };
-        if (bv.tile_w == 64 && bv.tile_h == 32) {
+        if (bv.tile_w == 64 && bv.tile_h == 32 && !tma_ws()) {
             constexpr int C = tma_ctas_per_sm<64, 32, 2>();
             stencil_tma_kernel<64, 32, 2><<<grid_for(C), tma_threads<64, 32, 2>(), TmaGeom<64, 32>::SMEM, s>>>(
                 bv.inst, bv.strips, bv.nstrips, stage);
@@ -1119,8 +1185,15 @@ cudaError_t launch_stencil(const BatchView &bv, int stage, int persistent_ctas, 
         }
         const int grid = grid_for(1);
         if (bv.tile_w == 64 && bv.tile_h == 60)
-            stencil_ws_kernel<64, 60, 2><<<grid, WsGeom<64, 60, 2>::NT, WsGeom<64, 60, 2>::SMEM, s>>>(
-                bv.inst, bv.strips, bv.nstrips, stage);
+            launch_ws<64, 60, 2, 2>(bv, stage, persistent_ctas, s);
+        else if (bv.tile_w == 64 && bv.tile_h == 40)
+            launch_ws<64, 40, 2, 3>(bv, stage, persistent_ctas, s);
+        else if (bv.tile_w == 64 && bv.tile_h == 24)
+            launch_ws<64, 24, 2, 2>(bv, stage, persistent_ctas, s);
+        else if (bv.tile_w == 128 && bv.tile_h == 28)
+            launch_ws<128, 28, 2, 2>(bv, stage, persistent_ctas, s);
+        else if (bv.tile_w == 64 && bv.tile_h == 32 && tma_ws())
+            launch_ws<64, 32, 2, 3>(bv, stage, persistent_ctas, s);
         else if (bv.tile_w == 128)
             stencil_tma_kernel<128, 32, 2><<<grid, tma_threads<128, 32, 2>(), TmaGeom<128, 32>::SMEM, s>>>(
                 bv.inst, bv.strips, bv.nstrips, stage);
@@ -1155,6 +1228,22 @@ cudaError_t launch_stencil(const BatchView &bv, int stage, int persistent_ctas, 
     }
     count_launch();
     return cudaGetLastError();
+}
+
+// name of the stencil kernel launch_stencil() picks for a batch view
+const char *stencil_kernel_name(const BatchView &bv) {
+    if (bv.precision == 1 && bv.kernel_mode == KERNEL_TMA) {
+        if (bv.tile_w == 64 && bv.tile_h == 32 && !tma_ws()) return "stencil_tma_kernel<64,32,2>";
+        if (bv.tile_w == 64 && bv.tile_h == 60) return "stencil_ws_kernel<64,60,2,2>";
+        if (bv.tile_w == 64 && bv.tile_h == 40) return "stencil_ws_kernel<64,40,2,3>";
+        if (bv.tile_w == 64 && bv.tile_h == 24) return "stencil_ws_kernel<64,24,2,2>";
+        if (bv.tile_w == 64 && bv.tile_h == 32) return "stencil_ws_kernel<64,32,2,3>";
+        if (bv.tile_w == 128 && bv.tile_h == 28) return "stencil_ws_kernel<128,28,2,2>";
+        if (bv.tile_w == 128) return "stencil_tma_kernel<128,32,2>";
+        return tma_rows() == 4 ? "stencil_tma_kernel<64,64,4>" : "stencil_tma_kernel<64,64,2>";
+    }
+    if (bv.kernel_mode == KERNEL_DIRECT) return bv.precision == 1 ? "stencil_kernel<float,true>" : "stencil_kernel<double,true>";
+    return bv.precision == 1 ? "stencil_kernel<float,false>" : "stencil_kernel<double,false>";
 }
 
 cudaError_t launch_probes(const BatchView &bv, cudaStream_t s) {

@@ -90,6 +90,7 @@ SIGNATURES = {
     "lee_batch_last_error": (C.c_char_p, [_vp]),
     "lee_batch_launch": (C.c_int, [_vp, C.c_int, C.c_int]),
     "lee_batch_status": (C.c_int, [_vp, _llp, C.c_int]),
+    "lee_batch_stencil_kernel": (C.c_char_p, [_vp]),
     "lee_energy_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, C.c_int, C.c_longlong, C.c_int, C.c_double,
                                       _vp, _vp]),
     "lee_launch_count": (C.c_longlong, []),
@@ -338,6 +339,10 @@ class Batch:
         out = np.zeros(max(n, 1), dtype=np.int64)
         self._c(self.L.lee_batch_status(self.b, out.ctypes.data_as(_llp), n))
         return out[:n]
+
+    def stencil_kernel(self):
+        """Name of the stencil kernel variant this batch launches."""
+        return (self.L.lee_batch_stencil_kernel(self.b) or b"").decode()
 
     def launch(self, stage, what):
         """Measurement hook: one ghost (what=0) or stencil (what=1) launch of a stage."""

@@ -218,3 +218,30 @@ def test_full_size_cylinder_1024(precision, cuda_device):
     count (3000 steps, FP64 and FP32 bulk with FP64 ghosts), compared over
     every fluid node, the ADE states and the probe ring."""
     _check(workloads.cylinder_pulse(1024), precision, steps=3000)
+
+
+def test_ghost_widening_paths_agree(cuda_device, tmp_path):
+    """The ghost kernel widens FP32 field values to FP64 on the integer pipe
+    (LEE_GHOST_WIDEN=int, the default) or with the hardware conversion
+    (LEE_GHOST_WIDEN=hw); both are exact, so the runs agree bitwise."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = (
+        "import sys, numpy as np\n"
+        "sys.path.insert(0, %r); sys.path.insert(0, %r)\n"
+        "from paper_2609_24785_b300 import workloads\n"
+        "from _helpers import make_solver\n"
+        "s = make_solver(workloads.flat_wall(128), 'fp32')\n"
+        "s.step(150); s.sync()\n"
+        "np.savez(sys.argv[1], p=s.field(0), u=s.field(1), v=s.field(2), x=s.ade())\n"
+    ) % (root, os.path.join(root, "tests"))
+    out = {}
+    for mode in ("hw", "int"):
+        f = str(tmp_path / ("%s.npz" % mode))
+        env = dict(os.environ, LEE_GHOST_WIDEN=mode)
+        subprocess.run([sys.executable, "-c", script, f], check=True, env=env, timeout=600)
+        out[mode] = np.load(f)
+    for k in ("p", "u", "v", "x"):
+        assert np.array_equal(out["hw"][k], out["int"][k]), k
