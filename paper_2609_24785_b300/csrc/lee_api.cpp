@@ -21,7 +21,6 @@ thread_local std::string g_create_err;
 
 constexpr size_t ALIGN = 256;
 inline size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
-constexpr int KERNELS_PER_STAGE = 2;
 constexpr int GRAPH_STEPS = 8;
 
 struct Layout {
@@ -78,7 +77,9 @@ struct lee_ctx {
     InstDesc *dd = nullptr;
     int *dprefix = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};   // [0]: 1 step, [1]: GRAPH_STEPS steps
+    long long graph_launches[2] = {0, 0};            // kernels per replay of each graph
     int nstrips = 0;
+    int nband = 0;                    // band nodes redone by band_kernel (warp-specialised stencil)
     std::string err;
     size_t elem() const { return g.precision == LEE_FP32 ? 4 : 8; }
 };
@@ -93,6 +94,7 @@ struct lee_batch {
     BatchView bv{};
     long long *status = nullptr;      // device: members' status words (lee_batch_status)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    long long graph_launches[2] = {0, 0};
     std::string err;
 };
 
@@ -197,8 +199,8 @@ cudaError_t enqueue_steps(const BatchView &bv, int steps, cudaStream_t s) {
 }
 
 // Run `nsteps` steps, capturing 1-step and GRAPH_STEPS-step graphs on first use.
-cudaError_t run_steps(const BatchView &bv, long long nsteps, cudaStream_t s, cudaGraphExec_t graph[2]) {
-    const int per_step = 4 * KERNELS_PER_STAGE + (bv.nprobe_inst > 0 ? 1 : 0);
+cudaError_t run_steps(const BatchView &bv, long long nsteps, cudaStream_t s, cudaGraphExec_t graph[2],
+                      long long graph_launches[2]) {
     static const bool no_graph = getenv("LEE_NO_GRAPH") != nullptr;
     if (s == nullptr || no_graph) {
         while (nsteps > 0) {
@@ -218,7 +220,8 @@ cudaError_t run_steps(const BatchView &bv, long long nsteps, cudaStream_t s, cud
         if (e != cudaSuccess) return e;
         const long long before = launch_count();
         e = enqueue_steps(bv, sizes[i], s);
-        count_launch(-(int)(launch_count() - before));        // replays are counted instead
+        graph_launches[i] = launch_count() - before;
+        count_launch(-(int)graph_launches[i]);                  // replays are counted instead
         cudaError_t e2 = cudaStreamEndCapture(s, &gr);
         if (e != cudaSuccess) return e;
         if (e2 != cudaSuccess) return e2;
@@ -229,13 +232,13 @@ cudaError_t run_steps(const BatchView &bv, long long nsteps, cudaStream_t s, cud
     while (nsteps >= GRAPH_STEPS && graph[1]) {
         cudaError_t e = cudaGraphLaunch(graph[1], s);
         if (e != cudaSuccess) return e;
-        count_launch(per_step * GRAPH_STEPS);
+        count_launch((int)graph_launches[1]);
         nsteps -= GRAPH_STEPS;
     }
     while (nsteps > 0) {
         cudaError_t e = cudaGraphLaunch(graph[0], s);
         if (e != cudaSuccess) return e;
-        count_launch(per_step);
+        count_launch((int)graph_launches[0]);
         --nsteps;
     }
     return cudaSuccess;
@@ -254,6 +257,8 @@ BatchView single_view(lee_ctx *c) {
     bv.kernel_mode = c->hd.kernel_mode;
     bv.tile_w = c->hd.tile_w;
     bv.tile_h = c->hd.tile_h;
+    bv.band_prefix = c->dprefix + 6;
+    bv.total_band = c->nband;
     bv.probe_inst = c->dprefix + 4;
     bv.nprobe_inst = c->hd.np > 0 ? 1 : 0;
     bv.total_tiles = c->hd.ntiles;
@@ -422,7 +427,12 @@ int lee_bind(lee_ctx *ctx, void *dev_ptr, long long dev_bytes, void *stream) {
         CK(cudaMemcpyAsync(ctx->dev + L.pi, pidx.data(), pidx.size() * 4, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(ctx->dev + L.pw, P.p_w.data(), P.p_w.size() * 8, cudaMemcpyHostToDevice, s));
     }
-    const int prefix[8] = {0, P.tiles_x * P.tiles_y, 0, ng, 0, 0, 0, 0};
+    // [0..1] tile prefix, [2..3] ghost prefix, [4] probe instance, [6..7] band-pass prefix
+    const int nband = uses_band_pass(ctx->g.precision, ctx->kernel_mode, P.tile_w, P.tile_h)
+                          ? band_nodes(P.nx, P.ny, ctx->g.bc_x == LEE_BC_PERIODIC, ctx->g.bc_y == LEE_BC_PERIODIC)
+                          : 0;
+    ctx->nband = nband;
+    const int prefix[8] = {0, P.tiles_x * P.tiles_y, 0, ng, 0, 0, 0, nband};
     CK(cudaMemcpyAsync(ctx->dev + L.prefix, prefix, sizeof prefix, cudaMemcpyHostToDevice, s));
     InstDesc &d = ctx->hd;
     d = InstDesc{};
@@ -533,7 +543,7 @@ int lee_step(lee_ctx *ctx, long long nsteps) {
     if (!ctx->bound) return fail(ctx, LEE_ERR_ARG, "lee_step before lee_bind");
     if (nsteps < 0) return fail(ctx, LEE_ERR_ARG, "nsteps < 0");
     if (nsteps == 0) return LEE_OK;
-    CK(run_steps(single_view(ctx), nsteps, ctx->stream, ctx->graph));
+    CK(run_steps(single_view(ctx), nsteps, ctx->stream, ctx->graph, ctx->graph_launches));
     return LEE_OK;
 }
 
@@ -751,7 +761,7 @@ static long long batch_bytes(const lee_batch *b) {
     size_t nch = 1, nst = 1;
     for (auto *c : b->members) { nch += n_chunks(c->hd.ng); nst += (size_t)c->hd.tiles_x * c->hd.tiles_y; }
     return (long long)(align_up(n * sizeof(InstDesc)) + 2 * align_up((n + 1) * 4) + align_up(nch * sizeof(int4)) +
-                       align_up(nst * sizeof(int4)) + align_up(n * sizeof(long long)));
+                       align_up(nst * sizeof(int4)) + align_up(n * sizeof(long long)) + align_up((n + 1) * 4));
 }
 
 int lee_batch_plan(lee_batch *b, long long *device_bytes) {
@@ -773,7 +783,7 @@ static int batch_refresh(lee_batch *b) {
     const size_t n = b->members.size();
     if (batch_bytes(b) > b->bytes) { b->err = "batch buffer too small"; return LEE_ERR_BUDGET; }
     std::vector<InstDesc> descs(n);
-    std::vector<int> tp(n + 1, 0), pi;
+    std::vector<int> tp(n + 1, 0), bp(n + 1, 0), pi;
     std::vector<int4> chunks, strips;
     int total_ghosts = 0;
     long long total_tiles = 0;
@@ -782,6 +792,7 @@ static int batch_refresh(lee_batch *b) {
     for (size_t i = 0; i < n; ++i) {
         descs[i] = b->members[i]->hd;
         tp[i + 1] = tp[i] + descs[i].ntiles;
+        bp[i + 1] = bp[i] + b->members[i]->nband;
         append_chunks(chunks, (int)i, descs[i].ng);
         append_strips(strips, (int)i, descs[i], seg);
         total_ghosts += descs[i].ng;
@@ -794,7 +805,8 @@ static int batch_refresh(lee_batch *b) {
     strips.resize(std::max<size_t>(strips.size(), 1));
     const size_t o_desc = 0, o_tp = align_up(n * sizeof(InstDesc)), o_pi = o_tp + align_up((n + 1) * 4),
                  o_ch = o_pi + align_up((n + 1) * 4), o_st = o_ch + align_up(chunks.size() * sizeof(int4)),
-                 o_status = o_st + align_up(strips.size() * sizeof(int4));
+                 o_status = o_st + align_up(strips.size() * sizeof(int4)),
+                 o_bp = o_status + align_up(n * sizeof(long long));
     b->status = (long long *)(b->dev + o_status);
     cudaError_t e;
     if (n) {
@@ -803,6 +815,7 @@ static int batch_refresh(lee_batch *b) {
             (e = cudaMemcpyAsync(b->dev + o_pi, pi.data(), pi.size() * 4, cudaMemcpyHostToDevice, b->stream)) ||
             (e = cudaMemcpyAsync(b->dev + o_ch, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream)) ||
             (e = cudaMemcpyAsync(b->dev + o_st, strips.data(), strips.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream)) ||
+            (e = cudaMemcpyAsync(b->dev + o_bp, bp.data(), (n + 1) * 4, cudaMemcpyHostToDevice, b->stream)) ||
             (e = cudaStreamSynchronize(b->stream))) {
             b->err = std::string("batch upload: ") + cudaGetErrorString(e);
             return LEE_ERR_CUDA;
@@ -820,6 +833,8 @@ static int batch_refresh(lee_batch *b) {
     bv.kernel_mode = n ? descs[0].kernel_mode : KERNEL_SMEM;
     bv.tile_w = n ? descs[0].tile_w : TILE_X;
     bv.tile_h = n ? descs[0].tile_h : TILE_Y;
+    bv.band_prefix = (const int *)(b->dev + o_bp);
+    bv.total_band = bp[n];
     bv.probe_inst = (const int *)(b->dev + o_pi);
     bv.nprobe_inst = 0;
     for (auto *c : b->members) bv.nprobe_inst += c->hd.np > 0;
@@ -839,7 +854,7 @@ int lee_batch_step(lee_batch *b, long long nsteps) {
         if (rc != LEE_OK) return rc;
     }
     if (b->members.empty() || nsteps <= 0) return LEE_OK;
-    cudaError_t e = run_steps(b->bv, nsteps, b->stream, b->graph);
+    cudaError_t e = run_steps(b->bv, nsteps, b->stream, b->graph, b->graph_launches);
     if (e != cudaSuccess) { b->err = std::string("batch step: ") + cudaGetErrorString(e); return LEE_ERR_CUDA; }
     return LEE_OK;
 }

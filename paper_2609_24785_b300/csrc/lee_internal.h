@@ -15,7 +15,7 @@ namespace lee {
 constexpr int TILE_X = 64;
 constexpr int TILE_Y = 32;
 constexpr int TMA_TILE_Y = 64;
-constexpr int GHOST_LANES = 4;          // lanes per ghost point in the ghost kernel
+constexpr int GHOST_LANES = 2;          // lanes per ghost point in the ghost kernel
 // stencil kernel variants
 constexpr int KERNEL_SMEM = 0;          // threads stage the halo box in shared memory (64 x 32 tiles)
 constexpr int KERNEL_DIRECT = 1;        // interior tiles read global memory directly (64 x 32 tiles)
@@ -150,6 +150,8 @@ struct BatchView {
     int use_tma;
     int kernel_mode;
     int tile_w, tile_h;
+    const int *band_prefix;     // ninst + 1: band nodes per instance (band_kernel), prefix sums (device)
+    int total_band;             // 0: the stencil kernel does the band itself
     const int *probe_inst;      // instances with probes (device), nprobe_inst entries
     int nprobe_inst;
     int total_tiles;
@@ -171,6 +173,8 @@ cudaError_t launch_from_staging(const InstDesc *dinst, const InstDesc &h, int wh
 cudaError_t launch_energy(const InstDesc *dinst, const InstDesc &h, cudaStream_t s);
 cudaError_t launch_status_gather(const BatchView &bv, long long *out, cudaStream_t s);
 const char *stencil_kernel_name(const BatchView &bv);
+bool uses_band_pass(int precision, int kernel_mode, int tile_w, int tile_h);
+int band_nodes(int nx, int ny, int per_x, int per_y);
 long long launch_count();
 void count_launch(int n = 1);
 // message for lee_last_error(NULL) (entry points without a context)

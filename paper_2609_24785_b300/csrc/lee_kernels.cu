@@ -2,16 +2,22 @@
 // ghost-point IBM / ADE / 2D LEE method, for any number of instances per
 // launch.
 //
-//  ghost_kernel    steps 1-5 of Sec. 3.2, one warp per ghost point: gather of
-//                  the cloud (bulk precision), six FP64 projections with the
-//                  combined weight rows, the MSD ADE (Sec. 2.5), the ghost
-//                  values p, u, v and the ADE stage update.
-//  stencil_kernel  step 6 of Sec. 3.2: 7-point DRP derivatives (Sec. 2.2 Eq.
-//                  DRP_s) of the LEE (Sec. 2.1 Eq. 1) from a shared-memory halo
-//                  tile, one-sided stencils + radiation condition in the outer
-//                  band, source, and the 2N-storage stage update
-//                  Q(k) = Q(n) + alpha_k dt RHS(Q(k-1)).
-//  probe / init / staging / energy kernels: bookkeeping.
+//  ghost_kernel       steps 1-5 of Sec. 3.2, GHOST_LANES lanes per ghost point:
+//                     gather of the cloud (bulk precision), six FP64
+//                     projections with the combined weight rows, the MSD ADE
+//                     (Sec. 2.5), the ghost values p, u, v and the ADE update.
+//  stencil_ws_kernel  step 6 of Sec. 3.2 (FP32 bulk): 7-point DRP derivatives
+//                     (Sec. 2.2 Eq. DRP_s) of the LEE (Sec. 2.1 Eq. 1) from TMA
+//                     halo tiles, source, ramp and the 2N-storage stage update
+//                     Q(k) = Q(n) + alpha_k dt RHS(Q(k-1)); warp-specialised.
+//  band_kernel        the same stage for the fluid nodes of the three outer
+//                     layers (one-sided stencils + radiation condition), after
+//                     stencil_ws_kernel.
+//  stencil_kernel, stencil_tma_kernel
+//                     step 6 with the outer band included: shared-memory or
+//                     global halo tiles (FP64, periodic axes) and the earlier
+//                     3-stage TMA pipeline.
+//  probe / init / staging / energy / status kernels: bookkeeping.
 #include <atomic>
 #include <cstdio>
 #include <string>
@@ -245,17 +251,18 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b
 __device__ __forceinline__ float2 pair(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
 
-// One fluid node of the three outer layers: one-sided stencils (rows 0..2
-// from an edge) and the radiation condition
+// One fluid node (gx, gy) of the three outer layers: one-sided stencils (rows
+// 0..2 from an edge) and the radiation condition
 // dq/dt = -(cos th dq/dx + sin th dq/dy + q / (2 rho)), polar about the domain
-// centre, plus the ramp term.  (lx, ly) is tile-local; the box around the tile
-// holds HALO nodes on every side, enough for the 5-point one-sided rows.
+// centre, plus the ramp term.  Q(k-1) is read at (sr + j) * bs + sc + i for
+// offsets |i|, |j| <= 4 that stay inside the grid (a halo box with HALO nodes
+// around a tile, or the global planes); Q^n at (qx, qy) of qn.
 template <typename T>
-__device__ __forceinline__ void band_point(const T *sp, const T *su, const T *sv, const int bs, const QnSrc<T> &qn,
-                                           const InstDesc &d, T *out, int gx, int gy, int lx, int ly, const T *K) {
+__device__ __forceinline__ void band_point(const T *sp, const T *su, const T *sv, const int bs, int sr, int sc,
+                                           const QnSrc<T> &qn, int qx, int qy, const InstDesc &d, T *out, int gx,
+                                           int gy, const T *K) {
     const T inv_h = K[K_INVH], half_inv_h = T(0.5) * inv_h;
     const T ad = K[K_AD], sk_h = K[K_SK];
-    const int sr = HALO + ly, sc = HALO + lx;
     auto fxp = [&](int q) { return sp[sr * bs + sc + q]; };
     auto fxu = [&](int q) { return su[sr * bs + sc + q]; };
     auto fxv = [&](int q) { return sv[sr * bs + sc + q]; };
@@ -278,7 +285,7 @@ __device__ __forceinline__ void band_point(const T *sp, const T *su, const T *sv
     const T ru = -(ct * dudx + st * dudy + u0 * q2) - sg * u0;
     const T rv = -(ct * dvdx + st * dvdy + v0 * q2) - sg * v0;
     const long long o = (long long)gy * d.pitch + gx, plane = d.plane;
-    const long long oq = qn.at(lx, ly);
+    const long long oq = qn.at(qx, qy);
     out[o] = qn.p[oq] + ad * rp;
     out[plane + o] = qn.u[oq] + ad * ru;
     out[2 * plane + o] = qn.v[oq] + ad * rv;
@@ -301,7 +308,10 @@ __device__ __forceinline__ void band_point(const T *sp, const T *su, const T *sv
 // evaluated two columns per instruction; FP64: q = q^n + alpha dt RHS with
 // the DRP derivatives times 1/h.
 // QNG: Q^n is in global memory (FP32 then loads it into registers first).
-template <typename T, int RY, int FL, bool QNG>
+// SKIPBAND: band nodes are neither stored nor listed; band_kernel does them
+// after this kernel, reading Q^n there (stage 4 writes Q(4) over Q^n, so the
+// band nodes must keep their Q^n until then).
+template <typename T, int RY, int FL, bool QNG, bool SKIPBAND = false>
 __device__ __forceinline__ void tile_points(const T *sp, const T *su, const T *sv, const int bs, const QnSrc<T> &qn,
                                             const InstDesc &d, T *out, int xt, int yt, const T *K, T src, int txi,
                                             int tyi, unsigned short *wl_idx, int *wl_n) {
@@ -485,7 +495,7 @@ __device__ __forceinline__ void tile_points(const T *sp, const T *su, const T *s
                     out[o + q] = o0.v[q]; out[plane + o + q] = o1.v[q]; out[2 * plane + o + q] = o2.v[q];
                 } else if (cat[q] == 1) {
                     out[o + q] = T(0); out[plane + o + q] = T(0); out[2 * plane + o + q] = T(0);
-                } else if (cat[q] == 2) {
+                } else if (cat[q] == 2 && !SKIPBAND) {
                     // at most 4 RY entries per thread, 128 RY per warp
                     wl_idx[atomicAdd(wl_n, 1)] = (unsigned short)(((ly0 + r) << 8) | (lx0 + q));
                 }
@@ -493,12 +503,12 @@ __device__ __forceinline__ void tile_points(const T *sp, const T *su, const T *s
         }
     }
     }  // live
-    if (BAND) {
+    if (BAND && !SKIPBAND) {
         __syncwarp();
         const int n = *(volatile int *)wl_n;
         for (int i = threadIdx.x & 31; i < n; i += 32) {
             const int e = wl_idx[i], lx = e & 0xff, ly = e >> 8;
-            band_point<T>(sp, su, sv, bs, qn, d, out, xt + lx, yt + ly, lx, ly, K);
+            band_point<T>(sp, su, sv, bs, HALO + ly, HALO + lx, qn, lx, ly, d, out, xt + lx, yt + ly, K);
         }
         __syncwarp();
         if ((threadIdx.x & 31) == 0) *wl_n = 0;
@@ -520,6 +530,23 @@ __device__ __forceinline__ void tile_dispatch(uint32_t flags, const T *sp, const
     else
         tile_points<T, RY, TILE_BAND | TILE_MIXED | TILE_SPONGE, QNG>(sp, su, sv, bs, qn, d, out, xt, yt, K, src,
                                                                       txi, tyi, wl_idx, wl_n);
+}
+
+// Warp-specialised kernel: band nodes are left to band_kernel, which runs
+// right after, so band tiles classify their nodes only to skip those.
+template <int RY>
+__device__ __forceinline__ void tile_dispatch_ws(uint32_t flags, const float *sp, const float *su, const float *sv,
+                                                 const int bs, const QnSrc<float> &qn, const InstDesc &d, float *out,
+                                                 int xt, int yt, const float *K, float src, int txi, int tyi) {
+    constexpr int B = TILE_BAND | TILE_SPONGE, M = TILE_BAND | TILE_MIXED | TILE_SPONGE;
+    if (flags == 0)
+        tile_points<float, RY, 0, false>(sp, su, sv, bs, qn, d, out, xt, yt, K, src, txi, tyi, nullptr, nullptr);
+    else if (!(flags & TILE_MIXED))
+        tile_points<float, RY, B, false, true>(sp, su, sv, bs, qn, d, out, xt, yt, K, src, txi, tyi, nullptr,
+                                               nullptr);
+    else
+        tile_points<float, RY, M, false, true>(sp, su, sv, bs, qn, d, out, xt, yt, K, src, txi, tyi, nullptr,
+                                               nullptr);
 }
 
 // per-warp band lists: 128 RY entries per warp, zeroed counters
@@ -645,7 +672,11 @@ template <int TW, int TH, int RYT> __host__ __device__ constexpr int tma_threads
 template <int TW, int TH, int RYT> __host__ __device__ constexpr int tma_ctas_per_sm() {
     return (2 * TmaGeom<TW, TH>::SMEM + 8192 <= 227 * 1024 && tma_threads<TW, TH, RYT>() <= 256) ? 2 : 1;
 }
-constexpr int WAIT_SPINS = 1 << 20;
+// bounded mbarrier waits: each try_wait may suspend the thread for up to
+// WAIT_HINT_NS (it resumes as soon as the phase completes), at most WAIT_SPINS
+// times before the wait gives up (milliseconds if the hint is ignored)
+constexpr int WAIT_SPINS = 1 << 18;
+constexpr uint32_t WAIT_HINT_NS = 20000;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -658,9 +689,9 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(WAIT_HINT_NS)
         : "memory");
     return ok != 0;
 }
@@ -783,7 +814,7 @@ template <int TW, int TH, int RYT, int S_> struct WsGeom {
     static constexpr uint32_t STAGE_BYTES = HALO_BYTES + QN_BYTES;
     static constexpr size_t SMEM = STAGES * (size_t)STAGE_BYTES + 1024;
     // static shared memory: band lists, descriptors, barriers
-    static constexpr size_t STATIC = (NC / 32) * (128 * RYT * 2 + 4) + STAGES * (sizeof(InstDesc) + 40) + 320;
+    static constexpr size_t STATIC = STAGES * (sizeof(InstDesc) + 40) + 320;
     // two CTAs per SM when both fit in shared memory and the register file
     static constexpr int CTAS = (2 * (SMEM + STATIC + 1024) <= 228 * 1024 && 2 * NT * 128 <= 65536) ? 2 : 1;
     static_assert(NC % 32 == 0, "whole consumer warps");
@@ -814,11 +845,9 @@ stencil_ws_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ st
     __shared__ int4 info[S];           // (instance, x0, y0, flags) of the tile in each stage
     __shared__ float ssrc[S];          // source amplitude x stage forcing of that tile's instance
     __shared__ __align__(16) InstDesc sdesc[S];   // the tile's instance descriptor
-    __shared__ WarpLists<NCW, RYT> wl;
     __shared__ int s_ntiles;
     __shared__ volatile int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    wl.init();
     const int inb = stage_in(stage), outb = stage_out(stage);
     if (tid == 0) {
         int n = 0;
@@ -899,10 +928,47 @@ stencil_ws_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ st
             const float *qs = sp + 3 * BW * BH;
             qn = QnSrc<float>{qs, qs + TW * TH, qs + 2 * TW * TH, TW};
         }
-        tile_dispatch<float, RYT, false>((uint32_t)inf.w, sp, su, sv, BW, qn, d, (float *)d.q[outb], inf.y, inf.z,
-                                         stage_k<float>(d, stage), ssrc[b], txi, tyi, wl.idx[warp], &wl.n[warp]);
+        tile_dispatch_ws<RYT>((uint32_t)inf.w, sp, su, sv, BW, qn, d, (float *)d.q[outb], inf.y, inf.z,
+                              stage_k<float>(d, stage), ssrc[b], txi, tyi);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[b]);
+    }
+}
+
+// ---------------------------------------------------------------- band pass
+// Band node b of a non-periodic instance: rows 0..2 and ny-3..ny-1 over the
+// full width (6 nx nodes), then columns 0..2 and nx-3..nx-1 of rows 3..ny-4.
+int band_nodes(int nx, int ny, int per_x, int per_y) {
+    return (per_x || per_y || nx < 6 || ny < 6) ? 0 : 6 * nx + 6 * (ny - 6);
+}
+
+// After the warp-specialised stencil of a stage: every fluid node of the three
+// outer layers is redone by one thread (band_point on the global planes).
+template <typename T>
+__global__ void __launch_bounds__(256)
+band_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__restrict__ bprefix, int total, int stage) {
+    const int inb = stage_in(stage), outb = stage_out(stage);
+    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < total; w += gridDim.x * blockDim.x) {
+        const int ii = find_inst(bprefix, ninst, w);
+        const InstDesc &d = inst[ii];
+        const int nx = d.nx, ny = d.ny;
+        int b = w - __ldg(bprefix + ii), gx, gy;
+        if (b < 3 * nx) {
+            gy = b / nx; gx = b - gy * nx;
+        } else if (b < 6 * nx) {
+            b -= 3 * nx; gy = ny - 3 + b / nx; gx = b % nx;
+        } else {
+            b -= 6 * nx;
+            const int r = b / 6, c = b - 6 * r;
+            gy = 3 + r; gx = c < 3 ? c : nx - 6 + c;
+        }
+        if (d.mask[(long long)gy * d.pitch + gx] != 1) continue;
+        const T *P = (const T *)d.q[inb];
+        const T *Q0 = (const T *)d.q[0];
+        const long long plane = d.plane;
+        const QnSrc<T> qn{Q0, Q0 + plane, Q0 + 2 * plane, d.pitch};
+        band_point<T>(P, P + plane, P + 2 * plane, d.pitch, gy, gx, qn, gx, gy, d, (T *)d.q[outb], gx, gy,
+                      stage_k<T>(d, stage));
     }
 }
 
@@ -1069,6 +1135,11 @@ void launch_ws(const BatchView &bv, int stage, int persistent_ctas, cudaStream_t
     using W = WsGeom<TW, TH, RYT, S_>;
     const int grid = std::min(bv.nstrips, persistent_ctas > 0 ? persistent_ctas : W::CTAS * num_sms());
     stencil_ws_kernel<TW, TH, RYT, S_><<<grid, W::NT, W::SMEM, s>>>(bv.inst, bv.strips, bv.nstrips, stage);
+    if (bv.total_band > 0) {
+        const int blocks = std::min((bv.total_band + 255) / 256, 4 * num_sms());
+        band_kernel<float><<<blocks, 256, 0, s>>>(bv.inst, bv.ninst, bv.band_prefix, bv.total_band, stage);
+        count_launch();
+    }
 }
 
 cudaError_t prepare_kernels(int precision) {
@@ -1228,6 +1299,13 @@ cudaError_t launch_stencil(const BatchView &bv, int stage, int persistent_ctas, 
     }
     count_launch();
     return cudaGetLastError();
+}
+
+// the stencil variant is warp-specialised and leaves the band to band_kernel
+bool uses_band_pass(int precision, int kernel_mode, int tile_w, int tile_h) {
+    if (precision != 1 || kernel_mode != KERNEL_TMA) return false;
+    if (tile_w == 64) return tile_h == 60 || tile_h == 40 || tile_h == 24 || (tile_h == 32 && tma_ws());
+    return tile_w == 128 && tile_h == 28;
 }
 
 // name of the stencil kernel launch_stencil() picks for a batch view
