@@ -127,11 +127,28 @@ void orc_destroy(orc_t *o)
 
 const char *orc_error(orc_t *o) { return o->err; }
 
-/* FP32-storage emulation: round the stored field (stage results, ghost values,
- * initial field) to single precision, as any implementation that keeps the
- * bulk field in FP32 must.  Used to derive the FP32 error floor. */
+/* Reduced-storage emulation: round the stored field (stage results, ghost
+ * values, initial field) as any implementation that keeps the bulk field in a
+ * narrower format must.  mode 1: single precision (the FP32 error floor);
+ * mode 2: bfloat16, 8 significant bits rounded to nearest even, single
+ * precision's exponent range (subnormals on the 2^-133 grid; no value here
+ * comes near the overflow limit), for the storage-precision study. */
 void orc_set_f32_storage(orc_t *o, int on) { o->f32_storage = on; }
-static double stored(const orc_t *o, double v) { return o->f32_storage ? (double)(float)v : v; }
+static double round_bf16(double v)
+{
+    if (v == 0.0 || !isfinite(v)) return v;
+    if (fabs(v) < 0x1p-126) return nearbyint(v * 0x1p133) * 0x1p-133;   /* subnormal grid, 2^-133 */
+    int e;
+    double m = frexp(v, &e);            /* v = m 2^e, 0.5 <= |m| < 1 */
+    m = nearbyint(m * 256.0) / 256.0;   /* 8 significant bits, ties to even */
+    return ldexp(m, e);
+}
+static double stored(const orc_t *o, double v)
+{
+    if (o->f32_storage == 1) return (double)(float)v;
+    if (o->f32_storage == 2) return round_bf16(v);
+    return v;
+}
 
 void orc_set_none(orc_t *o) { o->wall = 0; }
 void orc_set_line(orc_t *o, double xw, double yw, double angle)

@@ -173,7 +173,11 @@ class Oracle:
 
     def set_f32_storage(self, on=True):
         """Emulate FP32 storage of the field (tolerance studies only)."""
-        self._L.orc_set_f32_storage(self._o, int(on))
+        self._L.orc_set_f32_storage(self._o, int(bool(on)))
+
+    def set_bf16_storage(self):
+        """Emulate bfloat16 storage of the field (precision study only)."""
+        self._L.orc_set_f32_storage(self._o, 2)
 
     def setup(self):
         rc = self._L.orc_setup(self._o)
