@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the tile / packing autotuner")
+    ap.add_argument("--tile", default=None, help="TMA tile WxH (skips the autotuner)")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-duration", type=float, default=0.05,
                     help="seconds of Poisson arrivals of the serving trace")
@@ -242,6 +244,19 @@ def run_lee(args):
 
     t_setup = time.perf_counter()
     cases, rejected, desc = workload_cases(args, rank, accept=accept)
+    # tile shape and work packing: autotuned on a sample of the workload (FP32)
+    tile, strips, tuned = None, 0, None
+    if args.precision == "fp32":
+        if args.tile:
+            tile = tuple(int(x) for x in args.tile.split("x"))
+        elif not args.no_tune:
+            from paper_2609_24785_b300 import autotune
+            t_tune = time.perf_counter()
+            res = autotune.tune(cases)
+            tile, strips = res.tile, res.strips_per_sm
+            tuned = res.as_dict()
+            tuned["seconds"] = round(time.perf_counter() - t_tune, 2)
+            torch.cuda.synchronize()
     stream = torch.cuda.Stream(device=dev)
     batch = lee.Batch(args.precision, stream=stream)
     solvers = []
@@ -250,6 +265,8 @@ def run_lee(args):
     def plan(case):
         s = lee.Solver(case.nx, case.ny, case.h, case.cfl, precision=args.precision)
         workloads.apply_to(case, s)
+        if tile:
+            s.set_tile(*tile)
         if len(case.probes) and case.wall[0] != "none":
             s.set_probes(case.probes, 4096)
         s.plan()
@@ -260,6 +277,8 @@ def run_lee(args):
         s.bind(stream=stream)
         workloads.apply_state(case, s)
         batch.add(s)
+    if strips:
+        batch.set_strips_per_sm(strips)
     t_setup = time.perf_counter() - t_setup
     fluid = sum(s.sizes.n_fluid for s in solvers)
     ghosts = sum(s.sizes.n_ghost for s in solvers)
@@ -386,7 +405,8 @@ def run_lee(args):
                        "fluid_nodes": int(fluid), "ghost_points": int(ghosts),
                        "ghost_dtype": "f64", "l2": "working set %.1f GB >> 126 MB L2, no flush" %
                        (sum(s.sizes.device_bytes for s in solvers) / 1e9),
-                       "parallelism": "replicas" if ws > 1 else "single GPU", "setup_s": round(t_setup, 2)},
+                       "parallelism": "replicas" if ws > 1 else "single GPU", "setup_s": round(t_setup, 2),
+                       "stencil_kernel": batch.stencil_kernel(), "autotune": tuned},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": batch.stencil_kernel() + " stage 2",

@@ -106,6 +106,12 @@ int lee_set_impedance(lee_ctx *ctx, double R, double M, double K);
 int lee_set_rigid(lee_ctx *ctx);
 
 /* ---- plan and bind ------------------------------------------------------ */
+/* Tile shape of the FP32 TMA stencil (columns x rows of outputs per tile),
+ * before lee_plan; 0, 0 restores the default.  Supported shapes: 128x28,
+ * 64x60, 64x40, 64x32 and 64x24 (warp-specialised kernel).  LEE_ERR_ARG for
+ * another shape, after lee_plan, or for FP64 / periodic instances (their
+ * shared-memory kernel has one shape).  Batch members must share the shape. */
+int lee_set_tile(lee_ctx *ctx, int tile_w, int tile_h);
 /* Host set-up (Sec. 3.1): mask, ghost set, boundary points, elliptical clouds,
  * FP64 Householder-QR least squares, Lagrange factors, combined weight rows;
  * ADE poles/residues (Sec. 2.5) and the RK4 stability check of the poles.
@@ -216,6 +222,11 @@ const char *lee_batch_last_error(const lee_batch *b);
  * bit 1 = a ghost, ADE or probe value became non-finite (diverged).  One small
  * gather kernel and one copy; LEE_ERR_ARG if n differs from the member count. */
 int lee_batch_status(lee_batch *b, long long *host, int n);
+/* Packing of the batch's stencil work: columns of tiles are cut into strips of
+ * at most ceil(total tiles / (strips x SMs)) tiles, dealt longest first to the
+ * persistent CTAs; more strips balance better, fewer keep more halo rows in
+ * L2 down a strip.  strips = 1..64, 0 restores the default (2). */
+int lee_batch_set_strips_per_sm(lee_batch *b, int strips);
 /* Name of the stencil kernel variant the batch launches (static string; ""
  * before lee_batch_bind or without members). */
 const char *lee_batch_stencil_kernel(lee_batch *b);

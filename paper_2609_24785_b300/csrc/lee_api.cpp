@@ -36,8 +36,9 @@ void append_strips(std::vector<int4> &out, int inst, const InstDesc &d, int seg)
         for (int ty = 0; ty < d.tiles_y; ty += seg)
             out.push_back(make_int4(inst, tx, ty, std::min(seg, d.tiles_y - ty)));
 }
-int strip_segment(long long total_tiles) {
-    return (int)std::max<long long>(1, (total_tiles + 2LL * num_sms() - 1) / (2LL * num_sms()));
+int strip_segment(long long total_tiles, int strips_per_sm = 2) {
+    const long long n = (long long)strips_per_sm * num_sms();
+    return (int)std::max<long long>(1, (total_tiles + n - 1) / n);
 }
 // longest strips first, dealt round-robin to the persistent CTAs
 void sort_strips(std::vector<int4> &s) {
@@ -80,6 +81,7 @@ struct lee_ctx {
     long long graph_launches[2] = {0, 0};            // kernels per replay of each graph
     int nstrips = 0;
     int nband = 0;                    // band nodes redone by band_kernel (warp-specialised stencil)
+    int tile_w_req = 0, tile_h_req = 0;   // lee_set_tile (0: the default shape)
     std::string err;
     size_t elem() const { return g.precision == LEE_FP32 ? 4 : 8; }
 };
@@ -93,6 +95,7 @@ struct lee_batch {
     bool dirty = true;
     BatchView bv{};
     long long *status = nullptr;      // device: members' status words (lee_batch_status)
+    int strips_per_sm = 2;            // lee_batch_set_strips_per_sm
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     long long graph_launches[2] = {0, 0};
     std::string err;
@@ -352,6 +355,19 @@ int lee_set_probes(lee_ctx *ctx, int n, const double *xy, int capacity) {
     return LEE_OK;
 }
 
+int lee_set_tile(lee_ctx *ctx, int tile_w, int tile_h) {
+    if (!ctx) return LEE_ERR_ARG;
+    if (ctx->planned) return fail(ctx, LEE_ERR_ARG, "the tile shape is fixed after lee_plan");
+    if (tile_w == 0 && tile_h == 0) { ctx->tile_w_req = ctx->tile_h_req = 0; return LEE_OK; }
+    const bool periodic = ctx->g.bc_x == LEE_BC_PERIODIC || ctx->g.bc_y == LEE_BC_PERIODIC;
+    if (default_kernel_mode(ctx->g.precision, periodic) != KERNEL_TMA)
+        return fail(ctx, LEE_ERR_ARG, "tile shapes are selectable for the FP32 TMA stencil only");
+    if (!tma_tile_supported(tile_w, tile_h)) return fail(ctx, LEE_ERR_ARG, "unsupported tile shape");
+    ctx->tile_w_req = tile_w;
+    ctx->tile_h_req = tile_h;
+    return LEE_OK;
+}
+
 int lee_plan(lee_ctx *ctx, lee_sizes *out) {
     if (!ctx || !out) return LEE_ERR_ARG;
     const lee_grid &g = ctx->g;
@@ -359,7 +375,10 @@ int lee_plan(lee_ctx *ctx, lee_sizes *out) {
     const bool periodic = g.bc_x == LEE_BC_PERIODIC || g.bc_y == LEE_BC_PERIODIC;
     ctx->kernel_mode = default_kernel_mode(g.precision, periodic);
     int tile_w = TILE_X, tile_h = TILE_Y;
-    if (ctx->kernel_mode == KERNEL_TMA) tma_tile(tile_w, tile_h);
+    if (ctx->kernel_mode == KERNEL_TMA) {
+        tma_tile(tile_w, tile_h);
+        if (ctx->tile_w_req) { tile_w = ctx->tile_w_req; tile_h = ctx->tile_h_req; }
+    }
     int rc = build_plan(g.nx, g.ny, g.h, g.x0, g.y0, g.bc_x == LEE_BC_PERIODIC, g.bc_y == LEE_BC_PERIODIC,
                         g.cfl * g.h, tile_w, tile_h, ctx->geo, ctx->imp, ctx->probe_xy, ctx->plan, err);
     if (rc != LEE_OK) return fail(ctx, rc, err);
@@ -788,7 +807,7 @@ static int batch_refresh(lee_batch *b) {
     int total_ghosts = 0;
     long long total_tiles = 0;
     for (auto *c : b->members) total_tiles += c->hd.ntiles;
-    const int seg = strip_segment(total_tiles);
+    const int seg = strip_segment(total_tiles, b->strips_per_sm);
     for (size_t i = 0; i < n; ++i) {
         descs[i] = b->members[i]->hd;
         tp[i + 1] = tp[i] + descs[i].ntiles;
@@ -875,6 +894,13 @@ int lee_batch_status(lee_batch *b, long long *host, int n) {
         b->err = std::string("batch status: ") + cudaGetErrorString(e);
         return LEE_ERR_CUDA;
     }
+    return LEE_OK;
+}
+
+int lee_batch_set_strips_per_sm(lee_batch *b, int strips) {
+    if (!b || strips < 0 || strips > 64) return LEE_ERR_ARG;
+    b->strips_per_sm = strips ? strips : 2;
+    b->dirty = true;
     return LEE_OK;
 }
 

@@ -174,6 +174,7 @@ cudaError_t launch_energy(const InstDesc *dinst, const InstDesc &h, cudaStream_t
 cudaError_t launch_status_gather(const BatchView &bv, long long *out, cudaStream_t s);
 const char *stencil_kernel_name(const BatchView &bv);
 bool uses_band_pass(int precision, int kernel_mode, int tile_w, int tile_h);
+bool tma_tile_supported(int tw, int th);
 int band_nodes(int nx, int ny, int per_x, int per_y);
 long long launch_count();
 void count_launch(int n = 1);

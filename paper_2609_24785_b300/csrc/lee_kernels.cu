@@ -1165,14 +1165,14 @@ cudaError_t prepare_kernels(int precision) {
     return setup_stencil_attr<double>();
 }
 
-// TMA tile of FP32 instances, LEE_TMA_TILE: warp-specialised kernel 128x28
-// (default: 512-byte rows), 64x60, 64x40, 64x32 or 64x24; LEE_TMA_WS=0:
+// TMA tile of FP32 instances, LEE_TMA_TILE: warp-specialised kernel 64x40
+// (default, three stages), 128x28, 64x60, 64x32 or 64x24; LEE_TMA_WS=0:
 // 64x64, 64x32 or 128x32
 void tma_tile(int &tw, int &th) {
     static int w = 0, h = 0;
     if (!w) {
         const char *e = getenv("LEE_TMA_TILE");
-        const std::string v = e ? e : (tma_ws() ? "128x28" : "64x64");
+        const std::string v = e ? e : (tma_ws() ? "64x40" : "64x64");
         if (v == "128x32") { w = 128; h = 32; }
         else if (v == "64x32") { w = 64; h = 32; }
         else if (v == "64x60") { w = 64; h = 60; }
@@ -1306,6 +1306,13 @@ bool uses_band_pass(int precision, int kernel_mode, int tile_w, int tile_h) {
     if (precision != 1 || kernel_mode != KERNEL_TMA) return false;
     if (tile_w == 64) return tile_h == 60 || tile_h == 40 || tile_h == 24 || (tile_h == 32 && tma_ws());
     return tile_w == 128 && tile_h == 28;
+}
+
+// tile shapes launch_stencil() dispatches for FP32 instances without periodic axes
+bool tma_tile_supported(int tw, int th) {
+    if (tma_ws())
+        return (tw == 128 && th == 28) || (tw == 64 && (th == 60 || th == 40 || th == 32 || th == 24));
+    return (tw == 64 && (th == 64 || th == 32)) || (tw == 128 && th == 32);
 }
 
 // name of the stencil kernel launch_stencil() picks for a batch view

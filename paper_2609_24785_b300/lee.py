@@ -58,6 +58,7 @@ SIGNATURES = {
     "lee_set_wall_cylinder": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double]),
     "lee_set_impedance": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double]),
     "lee_set_rigid": (C.c_int, [_vp]),
+    "lee_set_tile": (C.c_int, [_vp, C.c_int, C.c_int]),
     "lee_plan": (C.c_int, [_vp, C.POINTER(lee_sizes)]),
     "lee_bind": (C.c_int, [_vp, _vp, C.c_longlong, _vp]),
     "lee_init_pulse": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double, C.c_double]),
@@ -91,6 +92,7 @@ SIGNATURES = {
     "lee_batch_launch": (C.c_int, [_vp, C.c_int, C.c_int]),
     "lee_batch_status": (C.c_int, [_vp, _llp, C.c_int]),
     "lee_batch_stencil_kernel": (C.c_char_p, [_vp]),
+    "lee_batch_set_strips_per_sm": (C.c_int, [_vp, C.c_int]),
     "lee_energy_noalloc": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, C.c_int, C.c_longlong, C.c_int, C.c_double,
                                       _vp, _vp]),
     "lee_launch_count": (C.c_longlong, []),
@@ -183,6 +185,10 @@ class Solver:
         self._nprobe = len(xy) // 2
         self._c(self.L.lee_set_probes(self.ctx, self._nprobe, _d(xy), int(capacity)))
         return self
+
+    def set_tile(self, tile_w, tile_h):
+        """FP32 TMA stencil tile shape (before plan); (0, 0) = default."""
+        self._c(self.L.lee_set_tile(self.ctx, int(tile_w), int(tile_h))); return self
 
     def plan(self):
         s = lee_sizes()
@@ -339,6 +345,10 @@ class Batch:
         out = np.zeros(max(n, 1), dtype=np.int64)
         self._c(self.L.lee_batch_status(self.b, out.ctypes.data_as(_llp), n))
         return out[:n]
+
+    def set_strips_per_sm(self, strips):
+        """Stencil work packing: tile strips per SM (0 = default 2)."""
+        self._c(self.L.lee_batch_set_strips_per_sm(self.b, int(strips)))
 
     def stencil_kernel(self):
         """Name of the stencil kernel variant this batch launches."""

@@ -5,10 +5,12 @@ import oracle
 from paper_2609_24785_b300 import lee, workloads
 
 
-def make_solver(case, precision="fp64", bind=True, probe_capacity=None):
+def make_solver(case, precision="fp64", bind=True, probe_capacity=None, tile=None):
     s = lee.Solver(case.nx, case.ny, case.h, case.cfl, precision=precision,
                    periodic_x=case.periodic[0], periodic_y=case.periodic[1])
     workloads.apply_to(case, s)
+    if tile:
+        s.set_tile(*tile)
     if len(case.probes):
         s.set_probes(case.probes, probe_capacity or max(case.steps, 1))
     s.plan()

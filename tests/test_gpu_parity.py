@@ -245,3 +245,32 @@ def test_ghost_widening_paths_agree(cuda_device, tmp_path):
         out[mode] = np.load(f)
     for k in ("p", "u", "v", "x"):
         assert np.array_equal(out["hw"][k], out["int"][k]), k
+
+
+@pytest.mark.parametrize("tile", [(64, 40), (64, 24)])
+def test_selected_tile_shape_matches_oracle(tile, cuda_device):
+    """A non-default tile shape per context (lee_set_tile) through the same
+    kernels: the ragged cylinder case against the oracle."""
+    case = workloads.cylinder_pulse(256, nx=200, ny=136)
+    c = case.centre
+    case.wall = ("cyl", c[0], c[1], 20.3 * case.h)
+    case.init = ("pulse", c[0] + 40 * case.h, c[1] + 3 * case.h, 1.0, 4 * case.h)
+    s = make_solver(case, "fp32", tile=tile)
+    s.step(300)
+    s.sync()
+    o, fluid, qmax, xmax = run_oracle(case, 300)
+    f32, _, _, _ = run_oracle(case, 300, f32_storage=True)
+    floor = _errors(f32, o, fluid, qmax, xmax)
+    err = _errors(s, o, fluid, qmax, xmax)
+    assert err[0] <= max(TOL["fp32"], FP32_FLOOR_FACTOR * floor[0]), (tile, err, floor)
+    assert err[1] <= max(TOL["fp32"], FP32_FLOOR_FACTOR * floor[1]), (tile, err, floor)
+    assert err[2] <= max(TOL["fp32"], FP32_FLOOR_FACTOR * floor[2]), (tile, err, floor)
+
+
+def test_autotuner_returns_a_measured_configuration(cuda_device):
+    from paper_2609_24785_b300 import autotune
+    cases, _ = workloads.sweep(6, seed=11)
+    res = autotune.tune(cases, sample=4, tiles=((128, 28), (64, 60)), strips=(1, 4), reps=2)
+    assert res.tile in ((128, 28), (64, 60)) and res.strips_per_sm in (1, 4)
+    assert len(res.table) == 4 and all(r["ms"] > 0 for r in res.table)
+    assert res.ns_per_node == min(r["ns_per_node"] for r in res.table)

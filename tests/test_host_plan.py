@@ -127,3 +127,36 @@ def test_probe_stencils_match_oracle():
     workloads.apply_to(case, o)
     o.setup()
     assert o.set_probes(case.probes, 4) == 0
+
+
+def test_tile_shape_selection():
+    """lee_set_tile: supported shapes change the plan's tile count; other
+    shapes, FP64 and periodic instances and calls after lee_plan are rejected."""
+    case = workloads.cylinder_pulse(256)
+    for tw, th in ((128, 28), (64, 60), (64, 24)):
+        s = lee.Solver(case.nx, case.ny, case.h, case.cfl, precision="fp32")
+        workloads.apply_to(case, s)
+        s.set_tile(tw, th)
+        assert s.plan().n_tiles == -(-case.nx // tw) * -(-case.ny // th)
+        with pytest.raises(lee.LeeError):
+            s.set_tile(64, 60)                                 # after lee_plan
+    s = lee.Solver(case.nx, case.ny, case.h, case.cfl, precision="fp32")
+    with pytest.raises(lee.LeeError):
+        s.set_tile(100, 28)
+    s.set_tile(0, 0)                                           # back to the default
+    s64 = lee.Solver(case.nx, case.ny, case.h, case.cfl, precision="fp64")
+    with pytest.raises(lee.LeeError):
+        s64.set_tile(128, 28)
+    sp = lee.Solver(case.nx, case.ny, case.h, case.cfl, precision="fp32", periodic_y=True)
+    with pytest.raises(lee.LeeError):
+        sp.set_tile(128, 28)
+
+
+def test_autotune_sample_is_size_stratified():
+    from paper_2609_24785_b300 import autotune
+    cases, _ = workloads.sweep(60, seed=7)
+    pick = autotune.stratified_sample(cases, 10)
+    sizes = sorted(c.nx for c in pick)
+    all_sizes = sorted(c.nx for c in cases)
+    assert len(pick) == 10 and sizes[0] == all_sizes[3] and sizes[-1] == all_sizes[57]
+    assert autotune.stratified_sample(cases[:5], 10) == cases[:5]
