@@ -342,11 +342,15 @@ def run_lee(args):
     peak, peak_kind = peaks()
     achieved = alg_bytes / (st_ms / 1e3) / 1e9
     traffic = None
+    kname = batch.stencil_kernel()
+    kname += (" + band_kernel" if kname.startswith("stencil_ws") else "") + " stage 2"
     tf = os.path.join(ROOT, "profiles", "stencil_traffic.json")
     if os.path.exists(tf):
         try:
             d = json.load(open(tf))
-            if d.get("workload") == desc and d.get("precision") == args.precision:
+            # counters of another kernel variant do not describe this one
+            if (d.get("workload") == desc and d.get("precision") == args.precision and
+                    d.get("kernel") == kname):
                 traffic = d.get("bytes_per_launch")
         except (ValueError, OSError):
             traffic = None
@@ -409,7 +413,7 @@ def run_lee(args):
                        "stencil_kernel": batch.stencil_kernel(), "autotune": tuned},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": batch.stencil_kernel() + " stage 2",
+                         "kernel": kname,
                          "launch_ms": st_ms, "alg_bytes_per_launch": int(alg_bytes),
                          "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else peak_kind},
             "ghost_kernel_ms": gh_ms,
