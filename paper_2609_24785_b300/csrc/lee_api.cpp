@@ -25,7 +25,7 @@ constexpr int GRAPH_STEPS = 8;
 
 struct Layout {
     size_t q, mask, tiles, gt, gs, gn, gk, ei, ew, xn, xs, gx, gy, pi, pw, ph, clock, scratch, staging, desc,
-        prefix, chunks, strips, tmap, total;
+        prefix, chunks, strips, tmap, bchunks, total;
 };
 
 // TMA stencil work list of one instance: columns of tiles (instance, tile
@@ -81,6 +81,7 @@ struct lee_ctx {
     long long graph_launches[2] = {0, 0};            // kernels per replay of each graph
     int nstrips = 0;
     int nband = 0;                    // band nodes redone by band_kernel (warp-specialised stencil)
+    int nbchunks = 0;                 // their band_kernel work-list entries
     int tile_w_req = 0, tile_h_req = 0;   // lee_set_tile (0: the default shape)
     std::string err;
     size_t elem() const { return g.precision == LEE_FP32 ? 4 : 8; }
@@ -119,6 +120,14 @@ void drop_graphs(cudaGraphExec_t g[2]) {
         if (g[i]) { cudaGraphExecDestroy(g[i]); g[i] = nullptr; }
 }
 
+// band nodes redone by band_kernel (0 unless the stencil leaves the band to it)
+int ctx_band_nodes(const lee_ctx *c) {
+    const Plan &P = c->plan;
+    return uses_band_pass(c->g.precision, c->kernel_mode, P.tile_w, P.tile_h)
+               ? band_nodes(P.nx, P.ny, c->g.bc_x == LEE_BC_PERIODIC, c->g.bc_y == LEE_BC_PERIODIC)
+               : 0;
+}
+
 Layout make_layout(const lee_ctx *c) {
     const Plan &P = c->plan;
     Layout L{};
@@ -152,6 +161,7 @@ Layout make_layout(const lee_ctx *c) {
     L.chunks = take((size_t)(n_chunks(ng) + 1) * sizeof(int4));
     L.strips = take((size_t)(P.tiles_x * P.tiles_y + 1) * sizeof(int4));
     L.tmap = take(4 * 128);
+    L.bchunks = take(((size_t)ctx_band_nodes(c) / 64 + 2) * sizeof(int4));
     L.total = o;
     return L;
 }
@@ -260,8 +270,8 @@ BatchView single_view(lee_ctx *c) {
     bv.kernel_mode = c->hd.kernel_mode;
     bv.tile_w = c->hd.tile_w;
     bv.tile_h = c->hd.tile_h;
-    bv.band_prefix = c->dprefix + 6;
-    bv.total_band = c->nband;
+    bv.band_chunks = (const int4 *)(c->dev + c->L.bchunks);
+    bv.nband_chunks = c->nbchunks;
     bv.probe_inst = c->dprefix + 4;
     bv.nprobe_inst = c->hd.np > 0 ? 1 : 0;
     bv.total_tiles = c->hd.ntiles;
@@ -446,12 +456,14 @@ int lee_bind(lee_ctx *ctx, void *dev_ptr, long long dev_bytes, void *stream) {
         CK(cudaMemcpyAsync(ctx->dev + L.pi, pidx.data(), pidx.size() * 4, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(ctx->dev + L.pw, P.p_w.data(), P.p_w.size() * 8, cudaMemcpyHostToDevice, s));
     }
-    // [0..1] tile prefix, [2..3] ghost prefix, [4] probe instance, [6..7] band-pass prefix
-    const int nband = uses_band_pass(ctx->g.precision, ctx->kernel_mode, P.tile_w, P.tile_h)
-                          ? band_nodes(P.nx, P.ny, ctx->g.bc_x == LEE_BC_PERIODIC, ctx->g.bc_y == LEE_BC_PERIODIC)
-                          : 0;
-    ctx->nband = nband;
-    const int prefix[8] = {0, P.tiles_x * P.tiles_y, 0, ng, 0, 0, 0, nband};
+    // [0..1] tile prefix, [2..3] ghost prefix, [4] probe instance
+    ctx->nband = ctx_band_nodes(ctx);
+    std::vector<int4> bch;
+    band_chunks(0, ctx->nband, bch);
+    ctx->nbchunks = (int)bch.size();
+    if (!bch.empty())
+        CK(cudaMemcpyAsync(ctx->dev + L.bchunks, bch.data(), bch.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+    const int prefix[8] = {0, P.tiles_x * P.tiles_y, 0, ng, 0, 0, 0, 0};
     CK(cudaMemcpyAsync(ctx->dev + L.prefix, prefix, sizeof prefix, cudaMemcpyHostToDevice, s));
     InstDesc &d = ctx->hd;
     d = InstDesc{};
@@ -777,10 +789,14 @@ int lee_batch_remove(lee_batch *b, lee_ctx *c) {
 
 static long long batch_bytes(const lee_batch *b) {
     const size_t n = std::max<size_t>(b->members.size(), 1);
-    size_t nch = 1, nst = 1;
-    for (auto *c : b->members) { nch += n_chunks(c->hd.ng); nst += (size_t)c->hd.tiles_x * c->hd.tiles_y; }
+    size_t nch = 1, nst = 1, nbc = 1;
+    for (auto *c : b->members) {
+        nch += n_chunks(c->hd.ng);
+        nst += (size_t)c->hd.tiles_x * c->hd.tiles_y;
+        nbc += c->nbchunks;
+    }
     return (long long)(align_up(n * sizeof(InstDesc)) + 2 * align_up((n + 1) * 4) + align_up(nch * sizeof(int4)) +
-                       align_up(nst * sizeof(int4)) + align_up(n * sizeof(long long)) + align_up((n + 1) * 4));
+                       align_up(nst * sizeof(int4)) + align_up(n * sizeof(long long)) + align_up(nbc * sizeof(int4)));
 }
 
 int lee_batch_plan(lee_batch *b, long long *device_bytes) {
@@ -802,7 +818,8 @@ static int batch_refresh(lee_batch *b) {
     const size_t n = b->members.size();
     if (batch_bytes(b) > b->bytes) { b->err = "batch buffer too small"; return LEE_ERR_BUDGET; }
     std::vector<InstDesc> descs(n);
-    std::vector<int> tp(n + 1, 0), bp(n + 1, 0), pi;
+    std::vector<int> tp(n + 1, 0), pi;
+    std::vector<int4> bch;
     std::vector<int4> chunks, strips;
     int total_ghosts = 0;
     long long total_tiles = 0;
@@ -811,7 +828,7 @@ static int batch_refresh(lee_batch *b) {
     for (size_t i = 0; i < n; ++i) {
         descs[i] = b->members[i]->hd;
         tp[i + 1] = tp[i] + descs[i].ntiles;
-        bp[i + 1] = bp[i] + b->members[i]->nband;
+        band_chunks((int)i, b->members[i]->nband, bch);
         append_chunks(chunks, (int)i, descs[i].ng);
         append_strips(strips, (int)i, descs[i], seg);
         total_ghosts += descs[i].ng;
@@ -825,7 +842,7 @@ static int batch_refresh(lee_batch *b) {
     const size_t o_desc = 0, o_tp = align_up(n * sizeof(InstDesc)), o_pi = o_tp + align_up((n + 1) * 4),
                  o_ch = o_pi + align_up((n + 1) * 4), o_st = o_ch + align_up(chunks.size() * sizeof(int4)),
                  o_status = o_st + align_up(strips.size() * sizeof(int4)),
-                 o_bp = o_status + align_up(n * sizeof(long long));
+                 o_bc = o_status + align_up(n * sizeof(long long));
     b->status = (long long *)(b->dev + o_status);
     cudaError_t e;
     if (n) {
@@ -834,7 +851,8 @@ static int batch_refresh(lee_batch *b) {
             (e = cudaMemcpyAsync(b->dev + o_pi, pi.data(), pi.size() * 4, cudaMemcpyHostToDevice, b->stream)) ||
             (e = cudaMemcpyAsync(b->dev + o_ch, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream)) ||
             (e = cudaMemcpyAsync(b->dev + o_st, strips.data(), strips.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream)) ||
-            (e = cudaMemcpyAsync(b->dev + o_bp, bp.data(), (n + 1) * 4, cudaMemcpyHostToDevice, b->stream)) ||
+            (bch.size() && (e = cudaMemcpyAsync(b->dev + o_bc, bch.data(), bch.size() * sizeof(int4),
+                                                cudaMemcpyHostToDevice, b->stream))) ||
             (e = cudaStreamSynchronize(b->stream))) {
             b->err = std::string("batch upload: ") + cudaGetErrorString(e);
             return LEE_ERR_CUDA;
@@ -852,8 +870,8 @@ static int batch_refresh(lee_batch *b) {
     bv.kernel_mode = n ? descs[0].kernel_mode : KERNEL_SMEM;
     bv.tile_w = n ? descs[0].tile_w : TILE_X;
     bv.tile_h = n ? descs[0].tile_h : TILE_Y;
-    bv.band_prefix = (const int *)(b->dev + o_bp);
-    bv.total_band = bp[n];
+    bv.band_chunks = (const int4 *)(b->dev + o_bc);
+    bv.nband_chunks = (int)bch.size();
     bv.probe_inst = (const int *)(b->dev + o_pi);
     bv.nprobe_inst = 0;
     for (auto *c : b->members) bv.nprobe_inst += c->hd.np > 0;

@@ -150,8 +150,8 @@ struct BatchView {
     int use_tma;
     int kernel_mode;
     int tile_w, tile_h;
-    const int *band_prefix;     // ninst + 1: band nodes per instance (band_kernel), prefix sums (device)
-    int total_band;             // 0: the stencil kernel does the band itself
+    const int4 *band_chunks;    // band_kernel work list (instance, first band node, count, 0) (device)
+    int nband_chunks;           // 0: the stencil kernel does the band itself
     const int *probe_inst;      // instances with probes (device), nprobe_inst entries
     int nprobe_inst;
     int total_tiles;
@@ -176,6 +176,7 @@ const char *stencil_kernel_name(const BatchView &bv);
 bool uses_band_pass(int precision, int kernel_mode, int tile_w, int tile_h);
 bool tma_tile_supported(int tw, int th);
 int band_nodes(int nx, int ny, int per_x, int per_y);
+void band_chunks(int inst, int nband, std::vector<int4> &out);
 long long launch_count();
 void count_launch(int n = 1);
 // message for lee_last_error(NULL) (entry points without a context)

@@ -21,6 +21,7 @@
 #include <atomic>
 #include <cstdio>
 #include <string>
+#include <vector>
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -257,18 +258,34 @@ __device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
 // centre, plus the ramp term.  Q(k-1) is read at (sr + j) * bs + sc + i for
 // offsets |i|, |j| <= 4 that stay inside the grid (a halo box with HALO nodes
 // around a tile, or the global planes); Q^n at (qx, qy) of qn.
-template <typename T>
+// PREFETCH (global planes): the 9-node x and y windows of p, u, v are loaded
+// into registers first (nodes outside the grid are skipped, never read), so
+// that all loads are in flight together instead of one derivative at a time.
+template <typename T, bool PREFETCH = false>
 __device__ __forceinline__ void band_point(const T *sp, const T *su, const T *sv, const int bs, int sr, int sc,
                                            const QnSrc<T> &qn, int qx, int qy, const InstDesc &d, T *out, int gx,
                                            int gy, const T *K) {
     const T inv_h = K[K_INVH], half_inv_h = T(0.5) * inv_h;
     const T ad = K[K_AD], sk_h = K[K_SK];
-    auto fxp = [&](int q) { return sp[sr * bs + sc + q]; };
-    auto fxu = [&](int q) { return su[sr * bs + sc + q]; };
-    auto fxv = [&](int q) { return sv[sr * bs + sc + q]; };
-    auto fyp = [&](int q) { return sp[(sr + q) * bs + sc]; };
-    auto fyu = [&](int q) { return su[(sr + q) * bs + sc]; };
-    auto fyv = [&](int q) { return sv[(sr + q) * bs + sc]; };
+    T wx[3][PREFETCH ? 9 : 1], wy[3][PREFETCH ? 9 : 1];
+    if constexpr (PREFETCH) {
+        const T *pl[3] = {sp, su, sv};
+#pragma unroll
+        for (int k = -4; k <= 4; ++k) {
+            const bool inx = gx + k >= 0 && gx + k < d.nx, iny = gy + k >= 0 && gy + k < d.ny;
+#pragma unroll
+            for (int f = 0; f < 3; ++f) {
+                wx[f][k + 4] = inx ? pl[f][(long long)sr * bs + sc + k] : T(0);
+                wy[f][k + 4] = iny ? pl[f][(long long)(sr + k) * bs + sc] : T(0);
+            }
+        }
+    }
+    auto fxp = [&](int q) { if constexpr (PREFETCH) return wx[0][q + 4]; else return sp[sr * bs + sc + q]; };
+    auto fxu = [&](int q) { if constexpr (PREFETCH) return wx[1][q + 4]; else return su[sr * bs + sc + q]; };
+    auto fxv = [&](int q) { if constexpr (PREFETCH) return wx[2][q + 4]; else return sv[sr * bs + sc + q]; };
+    auto fyp = [&](int q) { if constexpr (PREFETCH) return wy[0][q + 4]; else return sp[(sr + q) * bs + sc]; };
+    auto fyu = [&](int q) { if constexpr (PREFETCH) return wy[1][q + 4]; else return su[(sr + q) * bs + sc]; };
+    auto fyv = [&](int q) { if constexpr (PREFETCH) return wy[2][q + 4]; else return sv[(sr + q) * bs + sc]; };
     const T dpdx = deriv_general<T>(fxp, gx, d.nx, d.per_x, inv_h);
     const T dpdy = deriv_general<T>(fyp, gy, d.ny, d.per_y, inv_h);
     const T dudx = deriv_general<T>(fxu, gx, d.nx, d.per_x, inv_h);
@@ -276,11 +293,16 @@ __device__ __forceinline__ void band_point(const T *sp, const T *su, const T *sv
     const T dvdx = deriv_general<T>(fxv, gx, d.nx, d.per_x, inv_h);
     const T dvdy = deriv_general<T>(fyv, gy, d.ny, d.per_y, inv_h);
     const T rx = T(gx) - (T)d.cx, ryy = T(gy) - (T)d.cy;
-    const T rho = sqrt(rx * rx + ryy * ryy);
-    const T ct = rx / rho, st = ryy / rho;
-    const T q2 = half_inv_h / rho;                               // 1 / (2 h rho)
+    T ct, st, q2;                                                // cos th, sin th, 1 / (2 h rho)
+    if constexpr (sizeof(T) == 4) {
+        const float ri = rsqrtf(rx * rx + ryy * ryy);            // FP32: one reciprocal square root
+        ct = rx * ri; st = ryy * ri; q2 = half_inv_h * ri;
+    } else {
+        const T rho = sqrt(rx * rx + ryy * ryy);
+        ct = rx / rho; st = ryy / rho; q2 = half_inv_h / rho;
+    }
     const T sg = sk_h * ramp2<T>(d, gx, gy);
-    const T p0 = sp[sr * bs + sc], u0 = su[sr * bs + sc], v0 = sv[sr * bs + sc];
+    const T p0 = fxp(0), u0 = fxu(0), v0 = fxv(0);
     const T rp = -(ct * dpdx + st * dpdy + p0 * q2) - sg * p0;
     const T ru = -(ct * dudx + st * dudy + u0 * q2) - sg * u0;
     const T rv = -(ct * dvdx + st * dvdy + v0 * q2) - sg * v0;
@@ -938,21 +960,31 @@ stencil_ws_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ st
 // ---------------------------------------------------------------- band pass
 // Band node b of a non-periodic instance: rows 0..2 and ny-3..ny-1 over the
 // full width (6 nx nodes), then columns 0..2 and nx-3..nx-1 of rows 3..ny-4.
+constexpr int BAND_CHUNK = 128;             // band nodes per band_kernel block iteration
 int band_nodes(int nx, int ny, int per_x, int per_y) {
     return (per_x || per_y || nx < 6 || ny < 6) ? 0 : 6 * nx + 6 * (ny - 6);
 }
 
+// band_kernel work list of one instance: chunks of BAND_CHUNK band nodes,
+// (instance, first band node, count, 0), one per block iteration
+void band_chunks(int inst, int nband, std::vector<int4> &out) {
+    for (int f = 0; f < nband; f += BAND_CHUNK) out.push_back(make_int4(inst, f, std::min(BAND_CHUNK, nband - f), 0));
+}
+
 // After the warp-specialised stencil of a stage: every fluid node of the three
-// outer layers is redone by one thread (band_point on the global planes).
+// outer layers is redone by one thread (band_point on the global planes).  A
+// block takes whole chunks of one instance, so the instance is known before
+// any per-node load.
 template <typename T>
-__global__ void __launch_bounds__(256)
-band_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__restrict__ bprefix, int total, int stage) {
+__global__ void __launch_bounds__(BAND_CHUNK)
+band_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ chunks, int nchunks, int stage) {
     const int inb = stage_in(stage), outb = stage_out(stage);
-    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < total; w += gridDim.x * blockDim.x) {
-        const int ii = find_inst(bprefix, ninst, w);
-        const InstDesc &d = inst[ii];
+    for (int ci = blockIdx.x; ci < nchunks; ci += gridDim.x) {
+        const int4 ch = __ldg(chunks + ci);
+        if ((int)threadIdx.x >= ch.z) continue;
+        const InstDesc &d = inst[ch.x];
         const int nx = d.nx, ny = d.ny;
-        int b = w - __ldg(bprefix + ii), gx, gy;
+        int b = ch.y + threadIdx.x, gx, gy;
         if (b < 3 * nx) {
             gy = b / nx; gx = b - gy * nx;
         } else if (b < 6 * nx) {
@@ -962,13 +994,13 @@ band_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__restrict_
             const int r = b / 6, c = b - 6 * r;
             gy = 3 + r; gx = c < 3 ? c : nx - 6 + c;
         }
-        if (d.mask[(long long)gy * d.pitch + gx] != 1) continue;
+        if (__ldg(d.mask + (long long)gy * d.pitch + gx) != 1) continue;
         const T *P = (const T *)d.q[inb];
         const T *Q0 = (const T *)d.q[0];
         const long long plane = d.plane;
         const QnSrc<T> qn{Q0, Q0 + plane, Q0 + 2 * plane, d.pitch};
-        band_point<T>(P, P + plane, P + 2 * plane, d.pitch, gy, gx, qn, gx, gy, d, (T *)d.q[outb], gx, gy,
-                      stage_k<T>(d, stage));
+        band_point<T, true>(P, P + plane, P + 2 * plane, d.pitch, gy, gx, qn, gx, gy, d, (T *)d.q[outb], gx, gy,
+                            stage_k<T>(d, stage));
     }
 }
 
@@ -1135,9 +1167,9 @@ void launch_ws(const BatchView &bv, int stage, int persistent_ctas, cudaStream_t
     using W = WsGeom<TW, TH, RYT, S_>;
     const int grid = std::min(bv.nstrips, persistent_ctas > 0 ? persistent_ctas : W::CTAS * num_sms());
     stencil_ws_kernel<TW, TH, RYT, S_><<<grid, W::NT, W::SMEM, s>>>(bv.inst, bv.strips, bv.nstrips, stage);
-    if (bv.total_band > 0) {
-        const int blocks = std::min((bv.total_band + 255) / 256, 4 * num_sms());
-        band_kernel<float><<<blocks, 256, 0, s>>>(bv.inst, bv.ninst, bv.band_prefix, bv.total_band, stage);
+    if (bv.nband_chunks > 0) {
+        const int blocks = std::min(bv.nband_chunks, 8 * num_sms());
+        band_kernel<float><<<blocks, BAND_CHUNK, 0, s>>>(bv.inst, bv.band_chunks, bv.nband_chunks, stage);
         count_launch();
     }
 }
