@@ -1,0 +1,60 @@
+"""Convergence of the whole solver on the GPU (FP64 bulk): a pulse reflected by
+a cylinder, the same physical problem on 256^2, 512^2 and 1024^2 grids,
+compared with a 2048^2 run at the same physical times and probe positions.
+The paper measures about 3 on the impedance cylinder (Sec. 4).  The errors
+must fall at every refinement and the mean order over 256 -> 1024 must be at
+least 3.  Measured on a B300: rigid 5.0e-3, 2.0e-4, 4.2e-5 (orders 4.7, 2.2,
+mean 3.4); impedance 5.4e-3, 1.9e-4, 2.8e-5 (4.9, 2.7, mean 3.8)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2609_24785_b300 import workloads
+from _helpers import make_solver
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+L = 10.24                       # domain side (physical units)
+XC = 5.12 + 0.00137             # cylinder centre, off every grid's nodes
+R_CYL, W, XS_OFF = 0.5, 0.16, 1.0
+T_END = 1.6                     # the reflected pulse has crossed the probe ring
+
+
+def _case(n, rigid):
+    h = L / n
+    ang = np.arange(8) * math.pi / 4
+    probes = np.stack([XC + 1.5 * R_CYL * np.cos(ang), XC + 1.5 * R_CYL * np.sin(ang)], 1)
+    steps = int(round(T_END / (0.5 * h)))
+    return workloads.Case("conv_%d" % n, n, n, h=h, wall=("cyl", XC, XC, R_CYL),
+                          imp=("rigid",) if rigid else ("msd", 2.0, 0.02, 1.0),
+                          init=("pulse", XC + XS_OFF, XC, 1.0, W), probes=probes, steps=steps)
+
+
+def _probes(n, rigid, precision):
+    c = _case(n, rigid)
+    s = make_solver(c, precision)
+    s.step(c.steps)
+    s.sync()
+    return s.probes()                          # steps x 8, sample k at t = (k + 1) dt_n
+
+
+def _orders(rigid, precision):
+    ref = _probes(2048, rigid, precision)
+    errs = []
+    for n in (256, 512, 1024):
+        p = _probes(n, rigid, precision)
+        stride = 2048 // n                     # the fine run's samples at the coarse times
+        fine = ref[stride - 1::stride][:p.shape[0]]
+        errs.append(float(np.sqrt(np.mean((p - fine) ** 2)) / np.sqrt(np.mean(fine ** 2))))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    return errs, orders, math.log2(errs[0] / errs[2]) / 2
+
+
+@pytest.mark.parametrize("rigid", [True, False], ids=["rigid", "impedance"])
+def test_cylinder_pulse_converges(rigid, cuda_device):
+    errs, orders, mean = _orders(rigid, "fp64")
+    print("%s: relative probe errors %s, orders %s, mean %.2f" % (
+        "rigid" if rigid else "impedance", ["%.2e" % e for e in errs], ["%.2f" % o for o in orders], mean))
+    assert errs[0] > errs[1] > errs[2]
+    assert mean >= 3.0, (errs, orders)
