@@ -4,7 +4,8 @@
 Default workload: the batched cylinder-pulse sweep -- 512 independent solves,
 grid n^2 with n uniform in {256, 384, 512, 768, 1024}, cylinder radius 0.1 n,
 R, M, K log-uniform in [0.2, 5] x [0.005, 0.2] x [0.5, 20] (seed 24785), FP32
-field storage and stencils with FP64 ghost weights / ADE, advanced together by
+field storage and stencils with FP64 ghost weights / ADE (ghost projections in
+float-float on the FP32 pipe, about 48 significant bits), advanced together by
 one ghost launch and one stencil launch per Runge-Kutta stage (CUDA graph).
 A step is one time step (four stages) of every instance.  Metric: point-stage
 updates per second (fluid nodes x 4 stages x steps / time).  The device
@@ -56,6 +57,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the tile / packing autotuner")
     ap.add_argument("--tile", default=None, help="TMA tile WxH (skips the autotuner)")
+    ap.add_argument("--strips", type=int, default=0, help="tile strips per SM with --tile (0: library default)")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-duration", type=float, default=0.05,
                     help="seconds of Poisson arrivals of the serving trace")
@@ -249,6 +251,7 @@ def run_lee(args):
     if args.precision == "fp32":
         if args.tile:
             tile = tuple(int(x) for x in args.tile.split("x"))
+            strips = args.strips
         elif not args.no_tune:
             from paper_2609_24785_b300 import autotune
             t_tune = time.perf_counter()
@@ -349,9 +352,10 @@ def run_lee(args):
         try:
             d = json.load(open(tf))
             # counters of another kernel variant do not describe this one
-            if (d.get("workload") == desc and d.get("precision") == args.precision and
-                    d.get("kernel") == kname):
-                traffic = d.get("bytes_per_launch")
+            for e in d.get("entries", []):
+                if (e.get("workload") == desc and e.get("precision") == args.precision and
+                        e.get("kernel") == kname):
+                    traffic = e.get("bytes_per_launch")
         except (ValueError, OSError):
             traffic = None
 
@@ -407,7 +411,9 @@ def run_lee(args):
             "data": "synthetic",
             "config": {"workload": desc, "instances": len(cases), "rejected_unstable_draws": rejected,
                        "fluid_nodes": int(fluid), "ghost_points": int(ghosts),
-                       "ghost_dtype": "f64", "l2": "working set %.1f GB >> 126 MB L2, no flush" %
+                       "ghost_dtype": ("float-float (FP64 weights as FP32 pairs), f64 ADE"
+                                       if args.precision == "fp32" and os.environ.get("LEE_GHOST_ARITH") != "f64"
+                                       else "f64"), "l2": "working set %.1f GB >> 126 MB L2, no flush" %
                        (sum(s.sizes.device_bytes for s in solvers) / 1e9),
                        "parallelism": "replicas" if ws > 1 else "single GPU", "setup_s": round(t_setup, 2),
                        "stencil_kernel": batch.stencil_kernel(), "autotune": tuned},

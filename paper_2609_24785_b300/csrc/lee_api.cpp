@@ -425,6 +425,19 @@ int lee_bind(lee_ctx *ctx, void *dev_ptr, long long dev_bytes, void *stream) {
     const int ng = (int)P.g_target.size();
     const size_t plane = (size_t)P.ny * P.pitch;
     cudaStream_t s = ctx->stream;
+    // FP32 bulk: weights as float-float pairs for the FP32-pipe ghost gather
+    std::vector<GWF> wff;
+    if (ghost_float_float(ctx->g.precision)) {
+        wff.resize(P.e_w.size() / 4);
+        for (size_t e = 0; e < wff.size(); ++e)
+            for (int r = 0; r < 4; ++r) {
+                const double w = P.e_w[4 * e + r];
+                const float hi = (float)w;
+                if (!std::isfinite(hi)) return fail(ctx, LEE_ERR_GEOMETRY, "ghost weight outside the FP32 range");
+                wff[e].hi[r] = hi;
+                wff[e].lo[r] = (float)(w - (double)hi);     // w - hi is exact in FP64
+            }
+    }
     CK(prepare_kernels(ctx->g.precision));
     CK(cudaMemsetAsync(ctx->dev, 0, L.total, s));
     std::vector<int4> chunks;                 // ghost work list (after the memset above)
@@ -449,7 +462,10 @@ int lee_bind(lee_ctx *ctx, void *dev_ptr, long long dev_bytes, void *stream) {
         CK(cudaMemcpyAsync(ctx->dev + L.gn, gn.data(), (size_t)ng * 16, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(ctx->dev + L.gk, P.g_kappa.data(), (size_t)ng * 16, cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(ctx->dev + L.ei, ei.data(), ei.size() * 4, cudaMemcpyHostToDevice, s));
-        CK(cudaMemcpyAsync(ctx->dev + L.ew, P.e_w.data(), P.e_w.size() * 8, cudaMemcpyHostToDevice, s));
+        if (!wff.empty())
+            CK(cudaMemcpyAsync(ctx->dev + L.ew, wff.data(), wff.size() * sizeof(GWF), cudaMemcpyHostToDevice, s));
+        else
+            CK(cudaMemcpyAsync(ctx->dev + L.ew, P.e_w.data(), P.e_w.size() * 8, cudaMemcpyHostToDevice, s));
     }
     const int np = (int)ctx->probe_xy.size() / 2;
     if (np) {

@@ -51,6 +51,11 @@ void fill_stage_constants(double dt, double h, float kf[4][8], double kd[4][8]);
 // Combined FP64 weight row entry of one cloud node: p_BP = sum l0 p,
 // Neumann row wp, Dirichlet row wd, free-extrapolation row wf.
 struct alignas(32) GW { double l0, wp, wd, wf; };
+// The same 32 bytes for the float-float ghost kernel of the FP32 bulk: each
+// FP64 weight w as the pair w = hi + lo of FP32 numbers (hi = fl32(w),
+// lo = fl32(w - hi), 48 significant bits), the four hi parts first.
+struct alignas(32) GWF { float hi[4], lo[4]; };
+static_assert(sizeof(GWF) == sizeof(GW), "both weight layouts take 32 bytes per entry");
 
 // Per-instance descriptor read by every kernel (device copy in the arena;
 // copied whole into shared memory in 16-byte pieces by the TMA kernel).
@@ -73,7 +78,8 @@ struct alignas(16) InstDesc {
     const double2 *g_n;         // ng, wall normal (wall -> fluid)
     const double2 *g_kappa;     // ng, (kappa_p, kappa_u)
     const int *e_idx;           // entries: node index (j * pitch + i)
-    const GW *e_w;              // entries: (L0, w_p, w_d, w_f)
+    const GW *e_w;              // entries: (L0, w_p, w_d, w_f); GWF pairs when
+                                // ghost_float_float(precision) holds
     double *Xn;                 // ng x 2 ADE state at t_n
     double *Xs;                 // ng x 2 ADE state of the current stage
     double A[4], b[2], c[2];    // X' = A X + b p_BP, u_n = c . X
@@ -165,6 +171,9 @@ void tma_tile(int &tile_w, int &tile_h);
 // TMA descriptors of one FP32 instance (host encode; 4 x 128 bytes)
 bool encode_tensor_maps(const InstDesc &d, void *host_out /* 4 x 128 B */, std::string &err);
 cudaError_t launch_ghost(const BatchView &bv, int stage, cudaStream_t s);
+// FP32 bulk: the ghost projections run in float-float on the FP32 pipe and the
+// device weights are stored as GWF (LEE_GHOST_ARITH=f64 selects the FP64 gather)
+bool ghost_float_float(int precision);
 cudaError_t launch_stencil(const BatchView &bv, int stage, int persistent_ctas, cudaStream_t s);
 cudaError_t launch_probes(const BatchView &bv, cudaStream_t s);
 cudaError_t launch_init(const InstDesc *dinst, const InstDesc &h, int kind, const double *prm, cudaStream_t s);

@@ -3,8 +3,9 @@
 // launch.
 //
 //  ghost_kernel       steps 1-5 of Sec. 3.2, GHOST_LANES lanes per ghost point:
-//                     gather of the cloud (bulk precision), six FP64
-//                     projections with the combined weight rows, the MSD ADE
+//                     gather of the cloud (bulk precision), six projections
+//                     with the combined weight rows (FP64 sums; float-float
+//                     on the FP32 pipe for the FP32 bulk), the MSD ADE
 //                     (Sec. 2.5), the ghost values p, u, v and the ADE update.
 //  stencil_ws_kernel  step 6 of Sec. 3.2 (FP32 bulk): 7-point DRP derivatives
 //                     (Sec. 2.2 Eq. DRP_s) of the LEE (Sec. 2.1 Eq. 1) from TMA
@@ -87,12 +88,42 @@ __device__ __forceinline__ double widen_f32(float x) {
     }
     return __longlong_as_double((long long)(sign | bits));
 }
-template <bool INTW> __device__ __forceinline__ double to_f64(float x) { return INTW ? widen_f32(x) : (double)x; }
-template <bool INTW> __device__ __forceinline__ double to_f64(double x) { return x; }
+// gather arithmetic of ghost_kernel
+constexpr int GA_F64_HW = 0;    // FP64 sums, hardware FP32 -> FP64 conversion
+constexpr int GA_F64_INT = 1;   // FP64 sums, integer widening (widen_f32)
+constexpr int GA_FF = 2;        // float-float sums on the FP32 pipe (FP32 bulk)
+template <int GA> __device__ __forceinline__ double to_f64(float x) { return GA == GA_F64_INT ? widen_f32(x) : (double)x; }
+template <int GA> __device__ __forceinline__ double to_f64(double x) { return x; }
+
+// Float-float dot products (the compensated dot product "Dot2" of Ogita,
+// Rump and Oishi, SIAM J. Sci. Comput. 26, 2005), two rows per paired FP32
+// instruction.  The weight is the pair w = wh + wl; wh q is split exactly
+// into p + e (p = fl(wh q), e = fma(wh, q, -p)), fl(wl q) joins e, p enters
+// the running sum through Knuth's exact two-sum and every rounding error is
+// collected in the low word.  For n terms the error is about (n 2^-24)^2
+// sum|w q| + 2^-48 sum|w q|, against n 2^-53 sum|w q| for FP64 sums: both
+// far below the 2^-24 rounding of the stored ghost value.
+struct FF2 { float2 hi, lo; };
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ void two_sum_acc(FF2 &s, float2 p, float2 e) {
+    const float2 t = __fadd2_rn(s.hi, p);
+    const float2 bp = __fadd2_rn(t, neg2(s.hi));                 // the part of t that came from p
+    const float2 err = __fadd2_rn(__fadd2_rn(s.hi, neg2(__fadd2_rn(t, neg2(bp)))),
+                                  __fadd2_rn(p, neg2(bp)));      // s.hi + p - t, exactly
+    s.lo = __fadd2_rn(s.lo, __fadd2_rn(err, e));
+    s.hi = t;
+}
+__device__ __forceinline__ void ff_fma(FF2 &s, float2 wh, float2 wl, float2 q) {
+    const float2 p = __fmul2_rn(wh, q);
+    float2 e = __ffma2_rn(wh, q, neg2(p));                          // wh q - p, exactly
+    e = __ffma2_rn(wl, q, e);
+    two_sum_acc(s, p, e);
+}
+__device__ __forceinline__ double ff_value(float hi, float lo) { return (double)hi + (double)lo; }
 
 // One CTA handles GHOSTS_PER_CTA ghosts of one instance (a chunk of the work
 // list), GHOST_LANES lanes per ghost point.
-template <typename T, bool INTW>
+template <typename T, int GA>
 __global__ void __launch_bounds__(GHOST_THREADS)
 ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int4 *__restrict__ chunks, int nchunks,
              int stage) {
@@ -119,39 +150,84 @@ ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int4 *__restric
     T *P = (T *)d.q[stage_in(stage)];
     T *U = P + d.plane;
     T *V = P + 2 * d.plane;
-    double s0 = 0, s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0;
-    auto accumulate = [&](const GW &w, double p, double u, double v) {
-        s0 = fma(w.l0, p, s0);       // L0 . p      -> p_BP          (step 1)
-        s1 = fma(w.wp, p, s1);       // w_p . p     (Neumann row)
-        s2 = fma(w.wd, u, s2);       // w_d . u     (Dirichlet row)
-        s3 = fma(w.wd, v, s3);
-        s4 = fma(w.wf, u, s4);       // w_f . u     (free row)
-        s5 = fma(w.wf, v, s5);
-    };
-    // two entries per lane per round: all loads of both are issued first
-    int e = e0 + lane;
-    for (; e + GHOST_LANES < e1; e += 2 * GHOST_LANES) {
-        const int ia = __ldg(d.e_idx + e), ib = __ldg(d.e_idx + e + GHOST_LANES);
-        const GW wa = ldg_gw(d.e_w + e), wb = ldg_gw(d.e_w + e + GHOST_LANES);
-        const double pa = to_f64<INTW>(P[ia]), ua = to_f64<INTW>(U[ia]), va = to_f64<INTW>(V[ia]);
-        const double pb = to_f64<INTW>(P[ib]), ub = to_f64<INTW>(U[ib]), vb = to_f64<INTW>(V[ib]);
-        accumulate(wa, pa, ua, va);
-        accumulate(wb, pb, ub, vb);
-    }
-    if (e < e1) {
-        const int ia = __ldg(d.e_idx + e);
-        const GW wa = ldg_gw(d.e_w + e);
-        accumulate(wa, to_f64<INTW>(P[ia]), to_f64<INTW>(U[ia]), to_f64<INTW>(V[ia]));
-    }
     const unsigned gmask = ((1u << GHOST_LANES) - 1u) << (threadIdx.x & (32 - GHOST_LANES));
+    // rows: s0 = L0 . p -> p_BP (step 1), s1 = w_p . p (Neumann), s2, s3 =
+    // w_d . (u, v) (Dirichlet), s4, s5 = w_f . (u, v) (free)
+    double s0, s1, s2, s3, s4, s5;
+    if constexpr (GA == GA_FF) {
+        static_assert(sizeof(T) == 4, "float-float gather is for the FP32 bulk");
+        const float4 *W = reinterpret_cast<const float4 *>(d.e_w);
+        const float2 z = make_float2(0.f, 0.f);
+        FF2 a{z, z}, b{z, z}, c{z, z};                // (s0, s1), (s2, s3), (s4, s5)
+        auto accumulate = [&](const float4 &wh, const float4 &wl, float p, float u, float v) {
+            ff_fma(a, make_float2(wh.x, wh.y), make_float2(wl.x, wl.y), make_float2(p, p));
+            ff_fma(b, make_float2(wh.z, wh.z), make_float2(wl.z, wl.z), make_float2(u, v));
+            ff_fma(c, make_float2(wh.w, wh.w), make_float2(wl.w, wl.w), make_float2(u, v));
+        };
+        int e = e0 + lane;
+        for (; e + GHOST_LANES < e1; e += 2 * GHOST_LANES) {
+            const int ia = __ldg(d.e_idx + e), ib = __ldg(d.e_idx + e + GHOST_LANES);
+            const float4 wha = __ldg(W + 2 * e), wla = __ldg(W + 2 * e + 1);
+            const float4 whb = __ldg(W + 2 * (e + GHOST_LANES)), wlb = __ldg(W + 2 * (e + GHOST_LANES) + 1);
+            const float pa = P[ia], ua = U[ia], va = V[ia];
+            const float pb = P[ib], ub = U[ib], vb = V[ib];
+            accumulate(wha, wla, pa, ua, va);
+            accumulate(whb, wlb, pb, ub, vb);
+        }
+        if (e < e1) {
+            const int ia = __ldg(d.e_idx + e);
+            accumulate(__ldg(W + 2 * e), __ldg(W + 2 * e + 1), P[ia], U[ia], V[ia]);
+        }
 #pragma unroll
-    for (int o = GHOST_LANES / 2; o > 0; o >>= 1) {
-        s0 += __shfl_xor_sync(gmask, s0, o, GHOST_LANES);
-        s1 += __shfl_xor_sync(gmask, s1, o, GHOST_LANES);
-        s2 += __shfl_xor_sync(gmask, s2, o, GHOST_LANES);
-        s3 += __shfl_xor_sync(gmask, s3, o, GHOST_LANES);
-        s4 += __shfl_xor_sync(gmask, s4, o, GHOST_LANES);
-        s5 += __shfl_xor_sync(gmask, s5, o, GHOST_LANES);
+        for (int o = GHOST_LANES / 2; o > 0; o >>= 1) {
+            auto combine = [&](FF2 &s) {             // add the partner lane's pair
+                const float2 oh = make_float2(__shfl_xor_sync(gmask, s.hi.x, o, GHOST_LANES),
+                                              __shfl_xor_sync(gmask, s.hi.y, o, GHOST_LANES));
+                const float2 ol = make_float2(__shfl_xor_sync(gmask, s.lo.x, o, GHOST_LANES),
+                                              __shfl_xor_sync(gmask, s.lo.y, o, GHOST_LANES));
+                two_sum_acc(s, oh, ol);
+            };
+            combine(a);
+            combine(b);
+            combine(c);
+        }
+        s0 = ff_value(a.hi.x, a.lo.x); s1 = ff_value(a.hi.y, a.lo.y);
+        s2 = ff_value(b.hi.x, b.lo.x); s3 = ff_value(b.hi.y, b.lo.y);
+        s4 = ff_value(c.hi.x, c.lo.x); s5 = ff_value(c.hi.y, c.lo.y);
+    } else {
+        s0 = s1 = s2 = s3 = s4 = s5 = 0;
+        auto accumulate = [&](const GW &w, double p, double u, double v) {
+            s0 = fma(w.l0, p, s0);
+            s1 = fma(w.wp, p, s1);
+            s2 = fma(w.wd, u, s2);
+            s3 = fma(w.wd, v, s3);
+            s4 = fma(w.wf, u, s4);
+            s5 = fma(w.wf, v, s5);
+        };
+        // two entries per lane per round: all loads of both are issued first
+        int e = e0 + lane;
+        for (; e + GHOST_LANES < e1; e += 2 * GHOST_LANES) {
+            const int ia = __ldg(d.e_idx + e), ib = __ldg(d.e_idx + e + GHOST_LANES);
+            const GW wa = ldg_gw(d.e_w + e), wb = ldg_gw(d.e_w + e + GHOST_LANES);
+            const double pa = to_f64<GA>(P[ia]), ua = to_f64<GA>(U[ia]), va = to_f64<GA>(V[ia]);
+            const double pb = to_f64<GA>(P[ib]), ub = to_f64<GA>(U[ib]), vb = to_f64<GA>(V[ib]);
+            accumulate(wa, pa, ua, va);
+            accumulate(wb, pb, ub, vb);
+        }
+        if (e < e1) {
+            const int ia = __ldg(d.e_idx + e);
+            const GW wa = ldg_gw(d.e_w + e);
+            accumulate(wa, to_f64<GA>(P[ia]), to_f64<GA>(U[ia]), to_f64<GA>(V[ia]));
+        }
+#pragma unroll
+        for (int o = GHOST_LANES / 2; o > 0; o >>= 1) {
+            s0 += __shfl_xor_sync(gmask, s0, o, GHOST_LANES);
+            s1 += __shfl_xor_sync(gmask, s1, o, GHOST_LANES);
+            s2 += __shfl_xor_sync(gmask, s2, o, GHOST_LANES);
+            s3 += __shfl_xor_sync(gmask, s3, o, GHOST_LANES);
+            s4 += __shfl_xor_sync(gmask, s4, o, GHOST_LANES);
+            s5 += __shfl_xor_sync(gmask, s5, o, GHOST_LANES);
+        }
     }
     if (lane != 0) return;
     const double pbp = s0;
@@ -1168,13 +1244,33 @@ void launch_ws(const BatchView &bv, int stage, int persistent_ctas, cudaStream_t
     const int grid = std::min(bv.nstrips, persistent_ctas > 0 ? persistent_ctas : W::CTAS * num_sms());
     stencil_ws_kernel<TW, TH, RYT, S_><<<grid, W::NT, W::SMEM, s>>>(bv.inst, bv.strips, bv.nstrips, stage);
     if (bv.nband_chunks > 0) {
-        const int blocks = std::min(bv.nband_chunks, 8 * num_sms());
+        static const int per_sm = [] {
+            int n = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, band_kernel<float>, BAND_CHUNK, 0) != cudaSuccess || n < 1)
+                n = 1;
+            return n;
+        }();
+        const int blocks = std::min(bv.nband_chunks, per_sm * num_sms());
         band_kernel<float><<<blocks, BAND_CHUNK, 0, s>>>(bv.inst, bv.band_chunks, bv.nband_chunks, stage);
         count_launch();
     }
 }
 
+// LEE_L2_FETCH=32|64|128: the context's L2 fetch-granularity hint (bytes;
+// lasts as long as the process).  Measurement knob; unset leaves the default.
+static cudaError_t l2_fetch_hint() {
+    static const int bytes = [] {
+        const char *e = getenv("LEE_L2_FETCH");
+        return e ? atoi(e) : 0;
+    }();
+    static bool done = false;
+    if (done || bytes <= 0) return cudaSuccess;
+    done = true;
+    return cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)bytes);
+}
+
 cudaError_t prepare_kernels(int precision) {
+    if (cudaError_t e = l2_fetch_hint(); e != cudaSuccess) return e;
     if (precision == 1) {
         static bool done = false;
         if (!done) {
@@ -1256,18 +1352,28 @@ bool encode_tensor_maps(const InstDesc &d, void *host_out, std::string &err) {
     return true;
 }
 
+bool ghost_float_float(int precision) {
+    static const bool ff = [] {
+        const char *e = getenv("LEE_GHOST_ARITH");
+        return !(e && std::string(e) == "f64");
+    }();
+    return precision == 1 && ff;
+}
+
 cudaError_t launch_ghost(const BatchView &bv, int stage, cudaStream_t s) {
     const int blocks = bv.nchunks > 0 ? bv.nchunks : 1;
     static const bool intw = [] {
         const char *e = getenv("LEE_GHOST_WIDEN");
         return !(e && std::string(e) == "hw");
     }();
-    if (bv.precision == 1 && intw)
-        ghost_kernel<float, true><<<blocks, GHOST_THREADS, 0, s>>>(bv.inst, bv.ninst, bv.ghost_chunks, bv.nchunks, stage);
+    if (ghost_float_float(bv.precision))
+        ghost_kernel<float, GA_FF><<<blocks, GHOST_THREADS, 0, s>>>(bv.inst, bv.ninst, bv.ghost_chunks, bv.nchunks, stage);
+    else if (bv.precision == 1 && intw)
+        ghost_kernel<float, GA_F64_INT><<<blocks, GHOST_THREADS, 0, s>>>(bv.inst, bv.ninst, bv.ghost_chunks, bv.nchunks, stage);
     else if (bv.precision == 1)
-        ghost_kernel<float, false><<<blocks, GHOST_THREADS, 0, s>>>(bv.inst, bv.ninst, bv.ghost_chunks, bv.nchunks, stage);
+        ghost_kernel<float, GA_F64_HW><<<blocks, GHOST_THREADS, 0, s>>>(bv.inst, bv.ninst, bv.ghost_chunks, bv.nchunks, stage);
     else
-        ghost_kernel<double, false><<<blocks, GHOST_THREADS, 0, s>>>(bv.inst, bv.ninst, bv.ghost_chunks, bv.nchunks, stage);
+        ghost_kernel<double, GA_F64_HW><<<blocks, GHOST_THREADS, 0, s>>>(bv.inst, bv.ninst, bv.ghost_chunks, bv.nchunks, stage);
     count_launch();
     return cudaGetLastError();
 }

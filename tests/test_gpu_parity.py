@@ -148,6 +148,39 @@ def test_no_wall_and_small_grid(cuda_device):
     _check(case, "fp64")
 
 
+def _edge_cases():
+    """Grids with nx = 1, 2, 3 mod 4 (ragged last tile column) and 133, 64 and 3
+    rows between the top and bottom layers, pulses placed so that the waves
+    cross the outer layers within the run; a cylinder, a line wall crossing
+    both side columns (band nodes that are not fluid) and no wall."""
+    h = workloads.H
+    c1 = workloads.Case("edge_201x139", 201, 139, wall=("cyl", 100 * h, 69 * h, 15.3 * h),
+                        imp=("msd", 2.0, 0.02, 1.0), init=("pulse", 188.0 * h, 128.0 * h, 1.0, 3 * h),
+                        probes=np.array([[198.0 * h, 130.0 * h], [1.0 * h, 5.0 * h]]), steps=200)
+    c2 = workloads.Case("edge_202x70", 202, 70, wall=("line", 101.37 * h, 35.0 * h, math.radians(15.0)),
+                        imp=("msd", 1.0, 0.05, 5.0), init=("pulse", 60.0 * h, 45.0 * h, 1.0, 3 * h),
+                        probes=np.array([[2.0 * h, 30.0 * h]]), steps=200)
+    c3 = workloads.Case("edge_203x9", 203, 9, init=("pulse", 198.0 * h, 4.0 * h, 1.0, 2 * h),
+                        probes=np.array([[201.0 * h, 2.0 * h]]), steps=60)
+    return [c1, c2, c3]
+
+
+@pytest.mark.parametrize("case", _edge_cases(), ids=lambda c: c.name)
+def test_band_pass_ragged_edges_fp32(case, cuda_device):
+    """FP32 bulk: the outer three layers are done by the band pass after the
+    warp-specialised stencil; ragged tiles along both axes, masked edge nodes
+    and waves crossing the one-sided stencils and the radiation condition,
+    against the oracle."""
+    _check(case, "fp32")
+
+
+def test_small_grids_fp32(cuda_device):
+    """The band pass on grids with few interior rows (40 x 24: 18 rows between
+    the top and bottom layers; 8 x 8: 2)."""
+    _check(workloads.Case("free", 40, 24, init=("pulse", 0.2, 0.12, 1.0, 0.03), steps=50), "fp32")
+    _check(workloads.Case("tiny", 8, 8, init=("pulse", 0.035, 0.035, 1.0, 0.02), steps=20), "fp32")
+
+
 def test_energy_matches_oracle(cuda_device):
     case = workloads.cylinder_pulse(256)
     s = make_solver(case, "fp64")
@@ -220,10 +253,9 @@ def test_full_size_cylinder_1024(precision, cuda_device):
     _check(workloads.cylinder_pulse(1024), precision, steps=3000)
 
 
-def test_ghost_widening_paths_agree(cuda_device, tmp_path):
-    """The ghost kernel widens FP32 field values to FP64 on the integer pipe
-    (LEE_GHOST_WIDEN=int, the default) or with the hardware conversion
-    (LEE_GHOST_WIDEN=hw); both are exact, so the runs agree bitwise."""
+def _run_with_env(tmp_path, tag, env_over, case_expr, steps):
+    """Run one FP32 case in a child process (the kernel choice is read from
+    the environment once per process) and return its fields and ADE state."""
     import os
     import subprocess
     import sys
@@ -233,18 +265,43 @@ def test_ghost_widening_paths_agree(cuda_device, tmp_path):
         "sys.path.insert(0, %r); sys.path.insert(0, %r)\n"
         "from paper_2609_24785_b300 import workloads\n"
         "from _helpers import make_solver\n"
-        "s = make_solver(workloads.flat_wall(128), 'fp32')\n"
-        "s.step(150); s.sync()\n"
+        "s = make_solver(%s, 'fp32')\n"
+        "s.step(%d); s.sync()\n"
         "np.savez(sys.argv[1], p=s.field(0), u=s.field(1), v=s.field(2), x=s.ade())\n"
-    ) % (root, os.path.join(root, "tests"))
-    out = {}
-    for mode in ("hw", "int"):
-        f = str(tmp_path / ("%s.npz" % mode))
-        env = dict(os.environ, LEE_GHOST_WIDEN=mode)
-        subprocess.run([sys.executable, "-c", script, f], check=True, env=env, timeout=600)
-        out[mode] = np.load(f)
+    ) % (root, os.path.join(root, "tests"), case_expr, steps)
+    f = str(tmp_path / ("%s.npz" % tag))
+    subprocess.run([sys.executable, "-c", script, f], check=True, env=dict(os.environ, **env_over), timeout=600)
+    return np.load(f)
+
+
+def test_ghost_widening_paths_agree(cuda_device, tmp_path):
+    """The FP64 ghost gather widens FP32 field values to FP64 on the integer
+    pipe (LEE_GHOST_WIDEN=int, the default) or with the hardware conversion
+    (LEE_GHOST_WIDEN=hw); both are exact, so the runs agree bitwise."""
+    out = {mode: _run_with_env(tmp_path, mode, {"LEE_GHOST_ARITH": "f64", "LEE_GHOST_WIDEN": mode},
+                               "workloads.flat_wall(128)", 150) for mode in ("hw", "int")}
     for k in ("p", "u", "v", "x"):
         assert np.array_equal(out["hw"][k], out["int"][k]), k
+
+
+@pytest.mark.parametrize("case_expr", ["workloads.flat_wall(128)", "workloads.cylinder_pulse(256)"],
+                         ids=["flat_wall_128", "cylinder_256"])
+def test_float_float_ghost_gather_matches_fp64_gather(case_expr, cuda_device, tmp_path):
+    """FP32 bulk: the float-float ghost projections (the default) against the
+    FP64 ones (LEE_GHOST_ARITH=f64).  Their sums differ by about 1e-12 of the
+    summed magnitudes, so the FP32 ghost values they store are equal or one
+    unit in the last place apart: after one step the fields agree within a few
+    FP32 units of the field's largest value, after 200 steps within 1e-6 of
+    it (the linear update carries the single-unit differences, it does not
+    amplify them)."""
+    for steps, tol in ((1, 2.0 ** -21), (200, 1e-6)):
+        ff = _run_with_env(tmp_path, "ff%d" % steps, {}, case_expr, steps)
+        f64 = _run_with_env(tmp_path, "f64_%d" % steps, {"LEE_GHOST_ARITH": "f64"}, case_expr, steps)
+        for k in ("p", "u", "v"):
+            scale = max(float(np.abs(f64[k]).max()), 1e-30)
+            assert float(np.abs(ff[k] - f64[k]).max()) <= tol * scale, (steps, k)
+        xs = max(float(np.abs(f64["x"]).max()), 1e-30)
+        assert float(np.abs(ff["x"] - f64["x"]).max()) <= tol * xs, (steps, "ade")
 
 
 @pytest.mark.parametrize("tile", [(64, 40), (64, 24)])
