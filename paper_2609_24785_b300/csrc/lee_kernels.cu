@@ -121,10 +121,22 @@ __device__ __forceinline__ void ff_fma(FF2 &s, float2 wh, float2 wl, float2 q) {
 }
 __device__ __forceinline__ double ff_value(float hi, float lo) { return (double)hi + (double)lo; }
 
+// Asynchronous global -> shared copies (cp.async, 16 bytes through L2 only,
+// 4 bytes through L1): data is fetched early without holding registers.
+__device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
+                 "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *sdst, const void *gsrc) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
+                 "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // One CTA handles GHOSTS_PER_CTA ghosts of one instance (a chunk of the work
 // list), GHOST_LANES lanes per ghost point.
 template <typename T, int GA>
-__global__ void __launch_bounds__(GHOST_THREADS)
+__global__ void __launch_bounds__(GHOST_THREADS, GA == GA_FF ? 5 : 1)   // float-float: 5 CTAs per SM
 ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int4 *__restrict__ chunks, int nchunks,
              int stage) {
     if (stage == 1 && blockIdx.x == 0)
@@ -136,16 +148,29 @@ ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int4 *__restric
     const InstDesc &d = inst[ch.x];
     const int g = ch.y + sub;
     const int e0 = __ldg(d.g_start + g), e1 = __ldg(d.g_start + g + 1);
-    // per-ghost data, fetched before the gather so that the latencies overlap
+    // per-ghost data, fetched before the gather so that the latencies overlap:
+    // into registers (FP64 gathers), or by cp.async into shared memory
+    // (float-float gather, whose registers go to more resident warps)
+    constexpr int NSG = GA == GA_FF ? GHOSTS_PER_CTA : 1;
+    __shared__ __align__(16) double2 s_x[NSG], s_xn[NSG], s_n[NSG], s_k[NSG];
+    __shared__ int s_t[NSG];
     double x0 = 0, x1 = 0, xn0 = 0, xn1 = 0;
     double2 n = make_double2(0, 0), kap = make_double2(0, 0);
     int t = 0;
     if (lane == 0) {
-        x0 = d.Xs[2 * g]; x1 = d.Xs[2 * g + 1];
-        xn0 = d.Xn[2 * g]; xn1 = d.Xn[2 * g + 1];
-        n = __ldg(d.g_n + g);
-        kap = __ldg(d.g_kappa + g);
-        t = __ldg(d.g_target + g);
+        if constexpr (GA == GA_FF) {
+            cp_async16(&s_x[sub], d.Xs + 2 * g);            // 16-byte aligned: 2 doubles per ghost
+            cp_async16(&s_xn[sub], d.Xn + 2 * g);
+            cp_async16(&s_n[sub], d.g_n + g);
+            cp_async16(&s_k[sub], d.g_kappa + g);
+            cp_async4(&s_t[sub], d.g_target + g);
+        } else {
+            x0 = d.Xs[2 * g]; x1 = d.Xs[2 * g + 1];
+            xn0 = d.Xn[2 * g]; xn1 = d.Xn[2 * g + 1];
+            n = __ldg(d.g_n + g);
+            kap = __ldg(d.g_kappa + g);
+            t = __ldg(d.g_target + g);
+        }
     }
     T *P = (T *)d.q[stage_in(stage)];
     T *U = P + d.plane;
@@ -164,20 +189,25 @@ ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int4 *__restric
             ff_fma(b, make_float2(wh.z, wh.z), make_float2(wl.z, wl.z), make_float2(u, v));
             ff_fma(c, make_float2(wh.w, wh.w), make_float2(wl.w, wl.w), make_float2(u, v));
         };
+        // the cloud indices of the next round are loaded one round ahead, so
+        // that a round's gathers start without waiting for its index loads
         int e = e0 + lane;
+        int ia = e < e1 ? __ldg(d.e_idx + e) : 0;
+        int ib = e + GHOST_LANES < e1 ? __ldg(d.e_idx + e + GHOST_LANES) : 0;
         for (; e + GHOST_LANES < e1; e += 2 * GHOST_LANES) {
-            const int ia = __ldg(d.e_idx + e), ib = __ldg(d.e_idx + e + GHOST_LANES);
-            const float4 wha = __ldg(W + 2 * e), wla = __ldg(W + 2 * e + 1);
-            const float4 whb = __ldg(W + 2 * (e + GHOST_LANES)), wlb = __ldg(W + 2 * (e + GHOST_LANES) + 1);
+            const int en = e + 2 * GHOST_LANES;
+            const int na = en < e1 ? __ldg(d.e_idx + en) : 0;
+            const int nb = en + GHOST_LANES < e1 ? __ldg(d.e_idx + en + GHOST_LANES) : 0;
             const float pa = P[ia], ua = U[ia], va = V[ia];
             const float pb = P[ib], ub = U[ib], vb = V[ib];
+            const float4 wha = __ldg(W + 2 * e), wla = __ldg(W + 2 * e + 1);
+            const float4 whb = __ldg(W + 2 * (e + GHOST_LANES)), wlb = __ldg(W + 2 * (e + GHOST_LANES) + 1);
             accumulate(wha, wla, pa, ua, va);
             accumulate(whb, wlb, pb, ub, vb);
+            ia = na;
+            ib = nb;
         }
-        if (e < e1) {
-            const int ia = __ldg(d.e_idx + e);
-            accumulate(__ldg(W + 2 * e), __ldg(W + 2 * e + 1), P[ia], U[ia], V[ia]);
-        }
+        if (e < e1) accumulate(__ldg(W + 2 * e), __ldg(W + 2 * e + 1), P[ia], U[ia], V[ia]);
 #pragma unroll
         for (int o = GHOST_LANES / 2; o > 0; o >>= 1) {
             auto combine = [&](FF2 &s) {             // add the partner lane's pair
@@ -230,6 +260,14 @@ ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int4 *__restric
         }
     }
     if (lane != 0) return;
+    if constexpr (GA == GA_FF) {
+        cp_async_wait_all();                           // this thread's own copies
+        x0 = s_x[sub].x; x1 = s_x[sub].y;
+        xn0 = s_xn[sub].x; xn1 = s_xn[sub].y;
+        n = s_n[sub];
+        kap = s_k[sub];
+        t = s_t[sub];
+    }
     const double pbp = s0;
     // step 2: ADE derivative with p_BP as forcing
     const double xd0 = d.A[0] * x0 + d.A[1] * x1 + d.b[0] * pbp;
