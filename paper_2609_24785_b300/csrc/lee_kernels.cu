@@ -89,9 +89,11 @@ __device__ __forceinline__ double widen_f32(float x) {
     return __longlong_as_double((long long)(sign | bits));
 }
 // gather arithmetic of ghost_kernel
-constexpr int GA_F64_HW = 0;    // FP64 sums, hardware FP32 -> FP64 conversion
-constexpr int GA_F64_INT = 1;   // FP64 sums, integer widening (widen_f32)
-constexpr int GA_FF = 2;        // float-float sums on the FP32 pipe (FP32 bulk)
+enum GhostArith : int {
+    GA_F64_HW = 0,              // FP64 sums, hardware FP32 -> FP64 conversion
+    GA_F64_INT = 1,             // FP64 sums, integer widening (widen_f32)
+    GA_FF = 2                   // float-float sums on the FP32 pipe (FP32 bulk)
+};
 template <int GA> __device__ __forceinline__ double to_f64(float x) { return GA == GA_F64_INT ? widen_f32(x) : (double)x; }
 template <int GA> __device__ __forceinline__ double to_f64(double x) { return x; }
 
@@ -136,7 +138,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // One CTA handles GHOSTS_PER_CTA ghosts of one instance (a chunk of the work
 // list), GHOST_LANES lanes per ghost point.
 template <typename T, int GA>
-__global__ void __launch_bounds__(GHOST_THREADS, GA == GA_FF ? 5 : 1)   // float-float: 5 CTAs per SM
+__global__ void __launch_bounds__(GHOST_THREADS, GA == GA_FF ? 5 : 0)   // float-float: 5 CTAs per SM; others unconstrained
 ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int4 *__restrict__ chunks, int nchunks,
              int stage) {
     if (stage == 1 && blockIdx.x == 0)
