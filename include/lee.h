@@ -48,7 +48,7 @@ extern "C" {
 #define LEE_FP32 1
 
 /* outer boundary treatment per axis */
-#define LEE_BC_RADIATION 0      /* one-sided stencils + radiation condition in 3 layers */
+#define LEE_BC_RADIATION 0      /* one-sided DRP stencils + radiation condition in 3 layers */
 #define LEE_BC_PERIODIC  1
 
 /* field selectors */
@@ -104,6 +104,19 @@ int lee_set_wall_cylinder(lee_ctx *ctx, double xc, double yc, double r);
 int lee_set_impedance(lee_ctx *ctx, double R, double M, double K);
 /* Rigid wall, the limit Y -> 0: u_n = 0 and dp/dn = 0 (Sec. 2.4). */
 int lee_set_rigid(lee_ctx *ctx);
+/* Outer boundary of a non-periodic axis (Secs. 2.2, 4.1, 4.2): the three outer
+ * layers use the one-sided 7-point DRP stencils of Tam and Webb (1993) and
+ * their radiation condition dq/dt = -(cos th dq/dx + sin th dq/dy + q/(2 rho)),
+ * polar about the domain centre, with no damping, as in the paper.  That
+ * closure has grid-scale modes that grow by about 0.3% per step, so rounding
+ * errors become visible after several thousand steps (sooner in FP32).
+ * lee_set_sponge adds, as an opt-in departure from the paper, an absorbing
+ * ramp over the `width` outer layers: damping rate
+ * (kappa / h) ((width - d) / width)^2 at d < width cells from the nearest
+ * non-periodic edge (width 12, kappa 0.04 damp 2% per step at the edge at
+ * CFL 0.5).  width = 0 (the default) turns it off.  Before lee_plan;
+ * LEE_ERR_ARG for width < 0, kappa < 0 or a ramp wider than half the grid. */
+int lee_set_sponge(lee_ctx *ctx, int width, double kappa);
 
 /* ---- plan and bind ------------------------------------------------------ */
 /* Tile shape of the FP32 TMA stencil (columns x rows of outputs per tile),
@@ -200,6 +213,16 @@ int lee_ghost_info(lee_ctx *ctx, int g, int *target, double *meta, int *m, int *
  * p_BP = L0.p. */
 int lee_ghost_weights(lee_ctx *ctx, int g, int *idx, double *w, double *kappa);
 
+/* Steps 4-5 of Sec. 3.2 alone, through the product's ghost kernel: fill the
+ * ghost nodes of Q^n from given boundary data instead of the ADE's, with
+ * bc[2g] = u.n and bc[2g+1] = dp/dn at the boundary point of ghost g (normal
+ * from the wall into the fluid, ghost order of lee_ghost_info; n_ghost x 2
+ * host doubles, copied before the call returns).  Fluid nodes, ADE states and
+ * the step counter are untouched; synchronises the bound stream.  With exact
+ * boundary data of a polynomial field of degree <= 4 the ghost values equal
+ * the polynomial (Sec. 3.1).  LEE_ERR_ARG before lee_bind. */
+int lee_fill_ghosts_with_bc(lee_ctx *ctx, const double *bc);
+
 /* ---- batches: many instances per launch ---------------------------------- */
 /* A batch advances several bound contexts (any sizes, precisions must match)
  * with one ghost launch and one stencil launch per stage over all of them. */
@@ -252,8 +275,10 @@ int lee_batch_launch(lee_batch *b, int stage, int what);
  * library until the process exits.  ny > LEE_NOALLOC_MAX_ROWS is rejected with
  * LEE_ERR_ARG and a message (lee_last_error(NULL)).  The first call on a
  * device looks up the scratch's device address (cudaGetSymbolAddress) with
- * that device current, so make the first call on each device before any stream
- * capture.  All calls share the scratch; each call rewrites every entry it
+ * that device current and keeps it for the life of the process, so make the
+ * first call on each device before any stream capture, and do not reset a
+ * device (cudaDeviceReset) after its first call: the kept address would then
+ * be stale.  All calls share the scratch; each call rewrites every entry it
  * reads, so nothing needs clearing, but calls that overlap on the GPU (two
  * streams, two host threads) race on it.  The summation order is fixed: two
  * calls on the same data give bitwise the same result. */

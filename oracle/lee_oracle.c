@@ -18,14 +18,17 @@
  *   RK coefficients: 2N-storage Jameson alpha = (1/4, 1/3, 1/2, 1); a classical
  *   Butcher RK4 mode is kept for cross-checks.  The source time factor enters
  *   each stage as the moment of sin(w t) over the step that keeps the scheme
- *   4th order (stage_forcing).  One-sided stencils in the three outer layers: the
- *   4th-order 5-point Lagrange stencils (rows 0,1) and the central 5-point
- *   stencil (row 2).  Radiation condition in the three outer layers:
- *   dq/dt = -(cos th dq/dx + sin th dq/dy + q/(2 rho)), polar about the domain
- *   centre, no source there.  An absorbing ramp over the 12 outer layers
- *   (damping rate (0.04 c0/h) ((12 - d)/12)^2 at distance d from the edge,
- *   i.e. 2% per step at the edge for CFL 0.5) removes a slowly growing
- *   boundary mode of this closure.  Normal n points from the wall into the fluid;
+ *   4th order (stage_forcing).  One-sided stencils in the three outer layers:
+ *   the 7-point one-sided DRP stencils of Tam and Webb (J. Comput. Phys. 107,
+ *   1993), the scheme the paper cites for its boundary rows (Sec. 2.2), on
+ *   nodes 0..6 from the edge.  Radiation condition of Tam and Webb in the three
+ *   outer layers (Secs. 4.1-4.2): dq/dt = -(cos th dq/dx + sin th dq/dy +
+ *   q/(2 rho)), polar about the domain centre, no source there.  The paper adds
+ *   no damping (Sec. 4.3); an absorbing ramp over the W outer layers (rate
+ *   (kappa/h) ((W - d)/W)^2 at distance d from the edge) is available as an
+ *   opt-in departure (orc_set_sponge), off by default, for runs longer than
+ *   this closure stays stable: its semi-discrete operator has eigenvalues with
+ *   a small positive real part (grid-scale modes at the band).  Normal n points from the wall into the fluid;
  *   u_n (positive into the wall) = -u.n, so the Dirichlet datum for w = u.n is
  *   -u_n and the Neumann datum for dp/dn is +du_n/dt.  Critical damping uses
  *   the double-pole (Jordan) form of the same admittance.  A cloud clipped by
@@ -33,6 +36,9 @@
  *   cannot carry a plane (nodes on a single line) takes the constant fit (the
  *   cloud mean) with a linear normal extrapolation (m = 1).
  * Parity unpinned: none of the functions below (each has a pin in the tests).
+ * The one-sided stencil rows are pinned by their Taylor moments and by
+ * polynomial exactness; the band as a whole (one-sided rows + radiation
+ * condition) by the free-field Gaussian pulse against its exact solution.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -82,6 +88,10 @@ typedef struct {
     int n_reduced;              /* ghosts whose degree was lowered */
     const double *bc_override;  /* test hook: (w_BP, dp/dn_BP) per ghost */
     int f32_storage;            /* emulate FP32 storage of the field (tolerance studies) */
+    int sponge_w;               /* opt-in absorbing ramp: width in cells (0 = off) */
+    double sponge_k;            /* and strength kappa (rate kappa / h at the edge) */
+    double *work;               /* stage work arrays of orc_run (allocated once) */
+    size_t work_n;
     char err[256];
 } orc_t;
 
@@ -122,6 +132,7 @@ void orc_destroy(orc_t *o)
     free(o->kind);
     for (int f = 0; f < 3; f++) free(o->q[f]);
     free(o->pidx); free(o->pw); free(o->phist);
+    free(o->work);
     free(o);
 }
 
@@ -149,6 +160,11 @@ static double stored(const orc_t *o, double v)
     if (o->f32_storage == 2) return round_bf16(v);
     return v;
 }
+
+/* Opt-in absorbing ramp over the `width` outer layers of every non-periodic
+ * edge, damping rate (kappa / h) ((width - d) / width)^2 at distance d < width
+ * cells; width = 0 turns it off (the default, as in the paper). */
+void orc_set_sponge(orc_t *o, int width, double kappa) { o->sponge_w = width > 0 ? width : 0; o->sponge_k = kappa; }
 
 void orc_set_none(orc_t *o) { o->wall = 0; }
 void orc_set_line(orc_t *o, double xw, double yw, double angle)
@@ -401,8 +417,8 @@ static int wrap(int i, int n) { i %= n; return i < 0 ? i + n : i; }
 static void footprint(int i, int n, int per, int *lo, int *hi)
 {
     if (per) { *lo = i - 3; *hi = i + 3; return; }
-    if (i < 3) { *lo = 0; *hi = 4; return; }
-    if (i > n - 4) { *lo = n - 5; *hi = n - 1; return; }
+    if (i < 3) { *lo = 0; *hi = 6; return; }           /* one-sided rows read nodes 0..6 */
+    if (i > n - 4) { *lo = n - 7; *hi = n - 1; return; }
     *lo = i - 3; *hi = i + 3;
 }
 
@@ -653,24 +669,34 @@ long orc_get_probes(orc_t *o, double *out)
 }
 
 /* ------------------------------------------------------------ operator */
+/* One-sided 7-point DRP stencils of Tam and Webb (1993) for the three nodes
+ * nearest an edge: row r (node r from the edge) holds the coefficients of
+ * nodes 0..6, so that df/dx at node r = (1/h) sum_k TW[r][k] f_k.  Each row is
+ * exact for polynomials of degree <= 4 (to the 9 printed digits). */
+static const double ORC_TW[3][7] = {
+    {-2.192280339, 4.748611401, -5.108851915, 4.461567104, -2.833498741, 1.128328861, -0.203876371},
+    {-0.209337622, -1.084875676, 2.147776050, -1.388928322, 0.768949766, -0.281814650, 0.048230454},
+    {0.049041958, -0.468840357, -0.474760914, 1.273274737, -0.518484526, 0.166138533, -0.026369431}};
+
 /* First derivative along an axis of n nodes at index i, reading f[k * stride]
  * (k wrapped when the axis is periodic).  Sec. 2.2: the DRP stencil in the
- * interior; one-sided 4th-order stencils in the three outer layers of a
- * non-periodic axis (rows 0, 1: 5-point one-sided; row 2: 5-point central). */
+ * interior; the one-sided DRP stencils in the three outer layers of a
+ * non-periodic axis (at the far edge the mirror image: nodes n-1, n-2, ...
+ * with the signs reversed). */
 static double deriv1(const double *f, int stride, int n, int i, int per, double h)
 {
 #define F(k) f[(size_t)wrap((k), n) * stride]
     if (per || (i >= 3 && i <= n - 4))
         return (ORC_A1 * (F(i + 1) - F(i - 1)) + ORC_A2 * (F(i + 2) - F(i - 2)) +
                 ORC_A3 * (F(i + 3) - F(i - 3))) / h;
-    if (i == 0) return (-25.0 * F(0) + 48.0 * F(1) - 36.0 * F(2) + 16.0 * F(3) - 3.0 * F(4)) / (12.0 * h);
-    if (i == 1) return (-3.0 * F(0) - 10.0 * F(1) + 18.0 * F(2) - 6.0 * F(3) + F(4)) / (12.0 * h);
-    if (i == 2) return (F(0) - 8.0 * F(1) + 8.0 * F(3) - F(4)) / (12.0 * h);
-    if (i == n - 1)
-        return (25.0 * F(n - 1) - 48.0 * F(n - 2) + 36.0 * F(n - 3) - 16.0 * F(n - 4) + 3.0 * F(n - 5)) / (12.0 * h);
-    if (i == n - 2)
-        return (3.0 * F(n - 1) + 10.0 * F(n - 2) - 18.0 * F(n - 3) + 6.0 * F(n - 4) - F(n - 5)) / (12.0 * h);
-    return (F(n - 5) - 8.0 * F(n - 4) + 8.0 * F(n - 2) - F(n - 1)) / (12.0 * h);
+    double s = 0.0;
+    if (i < 3) {
+        for (int k = 0; k < 7; k++) s += ORC_TW[i][k] * F(k);
+    } else {
+        const int r = n - 1 - i;                 /* row counted from the far edge */
+        for (int k = 0; k < 7; k++) s -= ORC_TW[r][k] * F(n - 1 - k);
+    }
+    return s / h;
 #undef F
 }
 
@@ -686,19 +712,20 @@ void orc_deriv_1d(int n, const double *f, double h, int per, double *out)
     for (int i = 0; i < n; i++) out[i] = deriv1(f, 1, n, i, per, h);
 }
 
-/* Absorbing ramp near the non-periodic edges: damping rate at node (i, j),
- * (SPONGE_K / h) ((W - d) / W)^2 for a distance d < W (in cells) to the
- * nearest edge, 0 elsewhere. */
-#define SPONGE_W 12
-#define SPONGE_K 0.04
+/* Opt-in absorbing ramp near the non-periodic edges (off unless
+ * orc_set_sponge gave it a width W): damping rate at node (i, j),
+ * (kappa / h) ((W - d) / W)^2 for a distance d < W (in cells) to the nearest
+ * edge, 0 elsewhere. */
 static double sponge_rate(const orc_t *o, int i, int j)
 {
+    const int W = o->sponge_w;
+    if (W <= 0) return 0.0;
     int d = 1 << 30;
     if (!o->per_x) { if (i < d) d = i; if (o->nx - 1 - i < d) d = o->nx - 1 - i; }
     if (!o->per_y) { if (j < d) d = j; if (o->ny - 1 - j < d) d = o->ny - 1 - j; }
-    if (d >= SPONGE_W) return 0.0;
-    double r = (double)(SPONGE_W - d) / SPONGE_W;
-    return SPONGE_K / o->h * r * r;
+    if (d >= W) return 0.0;
+    double r = (double)(W - d) / W;
+    return o->sponge_k / o->h * r * r;
 }
 
 static int in_band(const orc_t *o, int i, int j)
@@ -797,16 +824,24 @@ void orc_run(orc_t *o, long nsteps, int classical)
     const size_t n = (size_t)o->nx * o->ny;
     const int ng = o->ng;
     const double dt = o->dt;
+    /* work arrays: allocated on the first call and kept, so that repeated
+     * short runs time the method and not the allocator */
+    size_t gx = 2 * (size_t)(ng > 0 ? ng : 1);
+    size_t need = 9 * n + 3 * gx;
+    if (o->work_n < need) {
+        free(o->work);
+        o->work = (double *)malloc(sizeof(double) * need);
+        o->work_n = need;
+    }
     double *qs[3], *rq[3], *acc[3];
     for (int f = 0; f < 3; f++) {
-        qs[f] = (double *)malloc(sizeof(double) * n);
-        rq[f] = (double *)malloc(sizeof(double) * n);
-        acc[f] = (double *)malloc(sizeof(double) * n);
+        qs[f] = o->work + (size_t)f * n;
+        rq[f] = o->work + (size_t)(3 + f) * n;
+        acc[f] = o->work + (size_t)(6 + f) * n;
     }
-    size_t gx = 2 * (size_t)(ng > 0 ? ng : 1);
-    double *Xs = (double *)malloc(sizeof(double) * gx);
-    double *Xd = (double *)malloc(sizeof(double) * gx);
-    double *Xacc = (double *)malloc(sizeof(double) * gx);
+    double *Xs = o->work + 9 * n;
+    double *Xd = Xs + gx;
+    double *Xacc = Xd + gx;
     static const double alpha[4] = {0.25, 1.0 / 3.0, 0.5, 1.0};
     for (long st = 0; st < nsteps; st++) {
         const double tn = (double)o->step * dt;
@@ -851,8 +886,6 @@ void orc_run(orc_t *o, long nsteps, int classical)
         o->step++;
         record_probes(o);
     }
-    for (int f = 0; f < 3; f++) { free(qs[f]); free(rq[f]); free(acc[f]); }
-    free(Xs); free(Xd); free(Xacc);
 }
 
 /* Fill the ghost nodes of the current Q^n from the current X^n (steps 1-5)

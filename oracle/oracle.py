@@ -61,6 +61,7 @@ def _load():
             "orc_set_monopole": (None, [vp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double]),
             "orc_setup": (C.c_int, [vp]),
             "orc_set_f32_storage": (None, [vp, C.c_int]),
+            "orc_set_sponge": (None, [vp, C.c_int, C.c_double]),
             "orc_n_ghost": (C.c_int, [vp]),
             "orc_n_reduced": (C.c_int, [vp]),
             "orc_regime": (C.c_int, [vp]),
@@ -174,6 +175,11 @@ class Oracle:
     def set_f32_storage(self, on=True):
         """Emulate FP32 storage of the field (tolerance studies only)."""
         self._L.orc_set_f32_storage(self._o, int(bool(on)))
+
+    def set_sponge(self, width, kappa=0.04):
+        """Opt-in absorbing ramp over `width` outer layers (0 = off, the default);
+        a departure from the paper, which adds no damping (Sec. 4.3)."""
+        self._L.orc_set_sponge(self._o, int(width), float(kappa))
 
     def set_bf16_storage(self):
         """Emulate bfloat16 storage of the field (precision study only)."""

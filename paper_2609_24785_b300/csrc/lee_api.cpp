@@ -25,7 +25,7 @@ constexpr int GRAPH_STEPS = 8;
 
 struct Layout {
     size_t q, mask, tiles, gt, gs, gn, gk, ei, ew, xn, xs, gx, gy, pi, pw, ph, clock, scratch, staging, desc,
-        prefix, chunks, strips, tmap, bchunks, total;
+        prefix, chunks, strips, tmap, bchunks, bc, total;
 };
 
 // TMA stencil work list of one instance: columns of tiles (instance, tile
@@ -83,6 +83,8 @@ struct lee_ctx {
     int nband = 0;                    // band nodes redone by band_kernel (warp-specialised stencil)
     int nbchunks = 0;                 // their band_kernel work-list entries
     int tile_w_req = 0, tile_h_req = 0;   // lee_set_tile (0: the default shape)
+    int sponge_w = 0;                 // lee_set_sponge: ramp width in cells (0: off)
+    double sponge_k = 0.0;            // and strength kappa
     std::string err;
     size_t elem() const { return g.precision == LEE_FP32 ? 4 : 8; }
 };
@@ -162,6 +164,7 @@ Layout make_layout(const lee_ctx *c) {
     L.strips = take((size_t)(P.tiles_x * P.tiles_y + 1) * sizeof(int4));
     L.tmap = take(4 * 128);
     L.bchunks = take(((size_t)ctx_band_nodes(c) / 64 + 2) * sizeof(int4));
+    L.bc = take((size_t)ng * 16);
     L.total = o;
     return L;
 }
@@ -356,6 +359,19 @@ int lee_set_rigid(lee_ctx *ctx) {
     return LEE_OK;
 }
 
+int lee_set_sponge(lee_ctx *ctx, int width, double kappa) {
+    if (!ctx) return LEE_ERR_ARG;
+    if (ctx->planned) return fail(ctx, LEE_ERR_ARG, "the absorbing ramp is fixed after lee_plan");
+    if (width < 0 || (width > 0 && !(kappa >= 0.0 && std::isfinite(kappa))))
+        return fail(ctx, LEE_ERR_ARG, "absorbing ramp needs width >= 0 and kappa >= 0");
+    const int nmin = std::min(ctx->g.bc_x == LEE_BC_PERIODIC ? 1 << 30 : ctx->g.nx,
+                              ctx->g.bc_y == LEE_BC_PERIODIC ? 1 << 30 : ctx->g.ny);
+    if (width > 0 && 2 * width > nmin) return fail(ctx, LEE_ERR_ARG, "absorbing ramp wider than half the grid");
+    ctx->sponge_w = width;
+    ctx->sponge_k = width > 0 ? kappa : 0.0;
+    return LEE_OK;
+}
+
 int lee_set_probes(lee_ctx *ctx, int n, const double *xy, int capacity) {
     if (!ctx) return LEE_ERR_ARG;
     if (ctx->planned) return fail(ctx, LEE_ERR_ARG, "probes are fixed after lee_plan");
@@ -390,7 +406,8 @@ int lee_plan(lee_ctx *ctx, lee_sizes *out) {
         if (ctx->tile_w_req) { tile_w = ctx->tile_w_req; tile_h = ctx->tile_h_req; }
     }
     int rc = build_plan(g.nx, g.ny, g.h, g.x0, g.y0, g.bc_x == LEE_BC_PERIODIC, g.bc_y == LEE_BC_PERIODIC,
-                        g.cfl * g.h, tile_w, tile_h, ctx->geo, ctx->imp, ctx->probe_xy, ctx->plan, err);
+                        g.cfl * g.h, tile_w, tile_h, ctx->sponge_w, ctx->geo, ctx->imp, ctx->probe_xy, ctx->plan,
+                        err);
     if (rc != LEE_OK) return fail(ctx, rc, err);
     if (ctx->plan.ade_amp > 1.0) {
         char b[160];
@@ -493,7 +510,8 @@ int lee_bind(lee_ctx *ctx, void *dev_ptr, long long dev_bytes, void *stream) {
     d.tile_w = P.tile_w;
     d.per_x = ctx->g.bc_x == LEE_BC_PERIODIC; d.per_y = ctx->g.bc_y == LEE_BC_PERIODIC;
     d.h = ctx->g.h; d.inv_h = 1.0 / ctx->g.h; d.dt = ctx->g.cfl * ctx->g.h;
-    fill_stage_constants(d.dt, d.h, d.kf, d.kd);
+    fill_stage_constants(d.dt, d.h, ctx->sponge_k, d.kf, d.kd);
+    d.sponge_w = ctx->sponge_w;
     d.cx = 0.5 * (P.nx - 1); d.cy = 0.5 * (P.ny - 1);
     d.ng = ng;
     d.g_target = (const int *)(ctx->dev + L.gt);
@@ -515,6 +533,7 @@ int lee_bind(lee_ctx *ctx, void *dev_ptr, long long dev_bytes, void *stream) {
     d.clock = (long long *)(ctx->dev + L.clock);
     d.scratch = (double *)(ctx->dev + L.scratch);
     d.staging = (double *)(ctx->dev + L.staging);
+    d.bc = (const double *)(ctx->dev + L.bc);
     d.precision = ctx->g.precision;
     d.kernel_mode = ctx->kernel_mode;
     d.use_tma = ctx->kernel_mode == KERNEL_TMA;
@@ -757,6 +776,18 @@ int lee_ghost_weights(lee_ctx *ctx, int g, int *idx, double *w, double *kappa) {
         if (w) for (int q = 0; q < 4; ++q) w[4 * (e - a) + q] = P.e_w[4 * (size_t)e + q];
     }
     if (kappa) { kappa[0] = P.g_kappa[2 * g]; kappa[1] = P.g_kappa[2 * g + 1]; }
+    return LEE_OK;
+}
+
+int lee_fill_ghosts_with_bc(lee_ctx *ctx, const double *bc) {
+    if (!ctx) return LEE_ERR_ARG;
+    if (!ctx->bound) return fail(ctx, LEE_ERR_ARG, "lee_fill_ghosts_with_bc before lee_bind");
+    const int ng = (int)ctx->plan.g_target.size();
+    if (ng == 0) return LEE_OK;
+    if (!bc) return fail(ctx, LEE_ERR_ARG, "null boundary data");
+    CK(cudaMemcpyAsync(ctx->dev + ctx->L.bc, bc, (size_t)ng * 16, cudaMemcpyHostToDevice, ctx->stream));
+    CK(launch_ghost(single_view(ctx), 0, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     return LEE_OK;
 }
 

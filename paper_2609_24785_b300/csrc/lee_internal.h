@@ -22,8 +22,9 @@ constexpr int KERNEL_DIRECT = 1;        // interior tiles read global memory dir
 constexpr int KERNEL_TMA = 2;           // FP32 TMA pipeline (64 x 64 tiles)
 constexpr int GHOST_THREADS = 256;
 constexpr int GHOSTS_PER_CTA = GHOST_THREADS / GHOST_LANES;
-constexpr int HALO = 4;                 // smem halo on each side (7-pt DRP needs 3,
-                                        // the 5-pt band stencils at the last row need 4)
+constexpr int HALO = 4;                 // smem halo on each side (the 7-pt DRP needs 3; 4 keeps
+                                        // the TMA box origin 16-byte aligned); band nodes read
+                                        // their one-sided windows from global memory
 constexpr int MAX_PROBES = 1024;
 
 // status word of an instance (InstDesc::clock[2]), set on the device
@@ -35,18 +36,18 @@ constexpr uint32_t TILE_BAND = 1u;      // output region meets the 3 outer layer
 constexpr uint32_t TILE_MIXED = 2u;     // has non-fluid or out-of-grid outputs
 constexpr uint32_t TILE_SPONGE = 4u;    // meets the absorbing ramp along the outer edges
 
-// Absorbing ramp along the non-periodic edges: damping rate
-// (SPONGE_K / h) ((SPONGE_W - d) / SPONGE_W)^2 at a distance d < SPONGE_W cells
-// from the nearest edge (2% per step at the edge for CFL 0.5).  It removes a
-// slowly growing mode of the one-sided/radiation closure on large domains.
-constexpr int SPONGE_W = 12;
-constexpr double SPONGE_K = 0.04;
+// Opt-in absorbing ramp along the non-periodic edges (lee_set_sponge; off by
+// default, as in the paper): damping rate (kappa / h) ((W - d) / W)^2 at a
+// distance d < W cells from the nearest edge.  It removes the slowly growing
+// grid-scale modes of the one-sided/radiation closure on long runs.
+constexpr int SPONGE_W_DEFAULT = 12;
+constexpr double SPONGE_K_DEFAULT = 0.04;
 
 // Per-stage constants of the bulk update of stage k (Sec. 3.2 step 6, Eq. 3):
-// alpha_k dt, alpha_k dt a_j / h (j = 1..3), alpha_k dt SPONGE_K / h, 1 / h,
-// SPONGE_K / h.
+// alpha_k dt, alpha_k dt a_j / h (j = 1..3), alpha_k dt kappa / h, 1 / h,
+// kappa / h (kappa = 0 without the ramp).
 enum { K_AD = 0, K_K1 = 1, K_K2 = 2, K_K3 = 3, K_KS = 4, K_INVH = 5, K_SK = 6 };
-void fill_stage_constants(double dt, double h, float kf[4][8], double kd[4][8]);
+void fill_stage_constants(double dt, double h, double kappa, float kf[4][8], double kd[4][8]);
 
 // Combined FP64 weight row entry of one cloud node: p_BP = sum l0 p,
 // Neumann row wp, Dirichlet row wd, free-extrapolation row wf.
@@ -99,7 +100,9 @@ struct alignas(16) InstDesc {
     long long *clock;           // [0] step in progress, [1] probe records, [2] status
     double *scratch;            // reductions
     double *staging;            // nx * ny doubles for host transfers
+    const double *bc;           // ng x 2 boundary data (u.n, dp/dn) of the ghost-fill test hook
     int precision;
+    int sponge_w;               // absorbing ramp width in cells (0: no ramp)
 };
 static_assert(sizeof(InstDesc) % 16 == 0, "InstDesc is copied in 16-byte pieces");
 
@@ -140,7 +143,7 @@ struct Impedance {
 
 // host set-up (lee_setup.cpp); returns LEE_* status, message in err
 int build_plan(int nx, int ny, double h, double x0, double y0, int per_x, int per_y, double dt, int tile_w, int tile_h,
-               const Geometry &geo, const Impedance &imp, const std::vector<double> &probe_xy,
+               int sponge_w, const Geometry &geo, const Impedance &imp, const std::vector<double> &probe_xy,
                Plan &plan, std::string &err);
 void stage_forcing_factors(double omega, double dt, double G_re[4], double G_im[4]);
 

@@ -136,7 +136,10 @@ __device__ __forceinline__ void cp_async4(void *sdst, const void *gsrc) {
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // One CTA handles GHOSTS_PER_CTA ghosts of one instance (a chunk of the work
-// list), GHOST_LANES lanes per ghost point.
+// list), GHOST_LANES lanes per ghost point.  stage 1..4: steps 1-5 of Sec. 3.2
+// for that stage.  stage 0 (test hook lee_fill_ghosts_with_bc): the ghosts of
+// Q^n are filled from the boundary data d.bc (u.n and dp/dn at each boundary
+// point) instead of the ADE's, and no ADE state or clock changes.
 template <typename T, int GA>
 __global__ void __launch_bounds__(GHOST_THREADS, GA == GA_FF ? 5 : 0)   // float-float: 5 CTAs per SM; others unconstrained
 ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int4 *__restrict__ chunks, int nchunks,
@@ -174,7 +177,7 @@ ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int4 *__restric
             t = __ldg(d.g_target + g);
         }
     }
-    T *P = (T *)d.q[stage_in(stage)];
+    T *P = (T *)d.q[stage == 0 ? 0 : stage_in(stage)];
     T *U = P + d.plane;
     T *V = P + 2 * d.plane;
     const unsigned gmask = ((1u << GHOST_LANES) - 1u) << (threadIdx.x & (32 - GHOST_LANES));
@@ -270,6 +273,16 @@ ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int4 *__restric
         kap = s_k[sub];
         t = s_t[sub];
     }
+    if (stage == 0) {                                  // test hook: given boundary data
+        const double wbp = d.bc[2 * g], dpdn = d.bc[2 * g + 1];
+        const double pg = s1 + kap.x * dpdn;
+        const double wg = n.x * s2 + n.y * s3 + kap.y * wbp;
+        const double tg = -n.y * s4 + n.x * s5;
+        P[t] = (T)pg;
+        U[t] = (T)(wg * n.x - tg * n.y);
+        V[t] = (T)(wg * n.y + tg * n.x);
+        return;
+    }
     const double pbp = s0;
     // step 2: ADE derivative with p_BP as forcing
     const double xd0 = d.A[0] * x0 + d.A[1] * x1 + d.b[0] * pbp;
@@ -312,29 +325,62 @@ __device__ __forceinline__ T drp(T m3, T m2, T m1, T p1, T p2, T p3) {
     return Drp<T>::a1 * (p1 - m1) + Drp<T>::a2 * (p2 - m2) + Drp<T>::a3 * (p3 - m3);
 }
 
-// derivative along one axis at absolute index x (axis length n) from smem
-// values f(k) = value at absolute index x + k; one-sided rows in the band
-template <typename T, typename F>
-__device__ __forceinline__ T deriv_general(F f, int x, int n, int per, T inv_h) {
-    if (per || (x >= 3 && x <= n - 4)) return drp<T>(f(-3), f(-2), f(-1), f(1), f(2), f(3)) * inv_h;
-    const T i12 = inv_h / T(12);
-    if (x == 0) return (T(-25) * f(0) + T(48) * f(1) - T(36) * f(2) + T(16) * f(3) - T(3) * f(4)) * i12;
-    if (x == 1) return (T(-3) * f(-1) - T(10) * f(0) + T(18) * f(1) - T(6) * f(2) + f(3)) * i12;
-    if (x == 2) return (f(-2) - T(8) * f(-1) + T(8) * f(1) - f(2)) * i12;
-    if (x == n - 1) return (T(25) * f(0) - T(48) * f(-1) + T(36) * f(-2) - T(16) * f(-3) + T(3) * f(-4)) * i12;
-    if (x == n - 2) return (T(3) * f(1) + T(10) * f(0) - T(18) * f(-1) + T(6) * f(-2) - f(-3)) * i12;
-    return (f(-2) - T(8) * f(-1) + T(8) * f(1) - f(2)) * i12;              // x == n - 3
+// Derivative rows of the band pass, one per position t of the node in its
+// 7-node window along the axis: t = 0, 1, 2 are the one-sided 7-point DRP
+// stencils of Tam and Webb (J. Comput. Phys. 107, 1993; the scheme Sec. 2.2
+// names for the three outer layers) at nodes 0, 1, 2 from the near edge, t = 3
+// the central DRP of Eq. DRP_s, t = 4, 5, 6 the mirror images of rows 2, 1, 0
+// at the far edge (row t, column j: -TW[6 - t][6 - j]).
+#define LEE_TW0 -2.192280339, 4.748611401, -5.108851915, 4.461567104, -2.833498741, 1.128328861, -0.203876371
+#define LEE_TW1 -0.209337622, -1.084875676, 2.147776050, -1.388928322, 0.768949766, -0.281814650, 0.048230454
+#define LEE_TW2 0.049041958, -0.468840357, -0.474760914, 1.273274737, -0.518484526, 0.166138533, -0.026369431
+#define LEE_BAND_ROWS                                                                                            \
+    {{LEE_TW0},                                                                                                  \
+     {LEE_TW1},                                                                                                  \
+     {LEE_TW2},                                                                                                  \
+     {-0.020843142770, 0.166705904415, -0.770882380518, 0.0, 0.770882380518, -0.166705904415, 0.020843142770}, \
+     {0.026369431, -0.166138533, 0.518484526, -1.273274737, 0.474760914, 0.468840357, -0.049041958},          \
+     {-0.048230454, 0.281814650, -0.768949766, 1.388928322, -2.147776050, 1.084875676, 0.209337622},          \
+     {0.203876371, -1.128328861, 2.833498741, -4.461567104, 5.108851915, -4.748611401, 2.192280339}}
+__constant__ double c_band_d[7][7] = LEE_BAND_ROWS;
+__constant__ float c_band_f[7][7] = LEE_BAND_ROWS;
+template <typename T> __device__ __forceinline__ T band_coef(int t, int j);
+template <> __device__ __forceinline__ float band_coef<float>(int t, int j) { return c_band_f[t][j]; }
+template <> __device__ __forceinline__ double band_coef<double>(int t, int j) { return c_band_d[t][j]; }
+
+// first node of the 7-node window of the derivative at index x of an axis of
+// n nodes (n >= 7) and the node's position t in it; periodic axes wrap
+__device__ __forceinline__ int band_window(int x, int n, int per, int &t) {
+    if (per) { t = 3; return x - 3; }
+    const int s = min(max(x - 3, 0), n - 7);
+    t = x - s;
+    return s;
 }
 
-// ((W - d) / W)^2 of the absorbing ramp at node (gx, gy), 0 outside it
-// (FP32: times the rounded 1 / W instead of a division)
+// sum_j C[t][j] (w_j - w_t) / h: the node's own value is taken out of every
+// term, which keeps the derivative of a constant exactly zero with rounded
+// coefficients
+template <typename T>
+__device__ __forceinline__ T band_deriv(const T (&w)[7], int t, T inv_h) {
+    const T wt = w[t];
+    T s = T(0);
+#pragma unroll
+    for (int j = 0; j < 7; ++j) s += band_coef<T>(t, j) * (w[j] - wt);
+    return s * inv_h;
+}
+
+// ((W - d) / W)^2 of the opt-in absorbing ramp (width W = d.sponge_w cells,
+// 0 = off) at node (gx, gy), 0 outside it (FP32: times the rounded 1 / W
+// instead of a division)
 template <typename T>
 __device__ __forceinline__ T ramp2(const InstDesc &d, int gx, int gy) {
+    const int W = d.sponge_w;
+    if (W <= 0) return T(0);
     int dist = 1 << 30;
     if (!d.per_x) dist = min(dist, min(gx, d.nx - 1 - gx));
     if (!d.per_y) dist = min(dist, min(gy, d.ny - 1 - gy));
-    if (dist >= SPONGE_W) return T(0);
-    const T r = sizeof(T) == 4 ? (T)(SPONGE_W - dist) * (T)(1.0f / SPONGE_W) : (T)(SPONGE_W - dist) / (T)SPONGE_W;
+    if (dist >= W) return T(0);
+    const T r = sizeof(T) == 4 ? (T)(W - dist) * (T)(1.0f / (float)W) : (T)(W - dist) / (T)W;
     return r * r;
 }
 
@@ -368,46 +414,37 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b
 __device__ __forceinline__ float2 pair(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
 
-// One fluid node (gx, gy) of the three outer layers: one-sided stencils (rows
-// 0..2 from an edge) and the radiation condition
+// One fluid node (gx, gy) of the three outer layers: one-sided DRP stencils
+// (rows 0..2 from an edge) and the radiation condition of Tam and Webb
 // dq/dt = -(cos th dq/dx + sin th dq/dy + q / (2 rho)), polar about the domain
-// centre, plus the ramp term.  Q(k-1) is read at (sr + j) * bs + sc + i for
-// offsets |i|, |j| <= 4 that stay inside the grid (a halo box with HALO nodes
-// around a tile, or the global planes); Q^n at (qx, qy) of qn.
-// PREFETCH (global planes): the 9-node x and y windows of p, u, v are loaded
-// into registers first (nodes outside the grid are skipped, never read), so
-// that all loads are in flight together instead of one derivative at a time.
-template <typename T, bool PREFETCH = false>
-__device__ __forceinline__ void band_point(const T *sp, const T *su, const T *sv, const int bs, int sr, int sc,
-                                           const QnSrc<T> &qn, int qx, int qy, const InstDesc &d, T *out, int gx,
-                                           int gy, const T *K) {
+// centre, plus the opt-in ramp term.  Q(k-1) is read from its global planes
+// gin (p; u at +plane; v at +2 plane): the 7-node x and y windows of p, u, v
+// are loaded first, all in flight together; Q^n at (qx, qy) of qn.
+template <typename T>
+__device__ __forceinline__ void band_point(const T *__restrict__ gin, const QnSrc<T> &qn, int qx, int qy,
+                                           const InstDesc &d, T *out, int gx, int gy, const T *K) {
     const T inv_h = K[K_INVH], half_inv_h = T(0.5) * inv_h;
     const T ad = K[K_AD], sk_h = K[K_SK];
-    T wx[3][PREFETCH ? 9 : 1], wy[3][PREFETCH ? 9 : 1];
-    if constexpr (PREFETCH) {
-        const T *pl[3] = {sp, su, sv};
+    const long long plane = d.plane, pitch = d.pitch;
+    int tx, ty;
+    const int sx = band_window(gx, d.nx, d.per_x, tx);
+    const int sy = band_window(gy, d.ny, d.per_y, ty);
+    T wx[3][7], wy[3][7];
 #pragma unroll
-        for (int k = -4; k <= 4; ++k) {
-            const bool inx = gx + k >= 0 && gx + k < d.nx, iny = gy + k >= 0 && gy + k < d.ny;
+    for (int k = 0; k < 7; ++k) {
+        int xk = sx + k, yk = sy + k;
+        if (d.per_x) xk = (xk % d.nx + d.nx) % d.nx;
+        if (d.per_y) yk = (yk % d.ny + d.ny) % d.ny;
+        const long long ox = (long long)gy * pitch + xk, oy = (long long)yk * pitch + gx;
 #pragma unroll
-            for (int f = 0; f < 3; ++f) {
-                wx[f][k + 4] = inx ? pl[f][(long long)sr * bs + sc + k] : T(0);
-                wy[f][k + 4] = iny ? pl[f][(long long)(sr + k) * bs + sc] : T(0);
-            }
+        for (int f = 0; f < 3; ++f) {
+            wx[f][k] = gin[f * plane + ox];
+            wy[f][k] = gin[f * plane + oy];
         }
     }
-    auto fxp = [&](int q) { if constexpr (PREFETCH) return wx[0][q + 4]; else return sp[sr * bs + sc + q]; };
-    auto fxu = [&](int q) { if constexpr (PREFETCH) return wx[1][q + 4]; else return su[sr * bs + sc + q]; };
-    auto fxv = [&](int q) { if constexpr (PREFETCH) return wx[2][q + 4]; else return sv[sr * bs + sc + q]; };
-    auto fyp = [&](int q) { if constexpr (PREFETCH) return wy[0][q + 4]; else return sp[(sr + q) * bs + sc]; };
-    auto fyu = [&](int q) { if constexpr (PREFETCH) return wy[1][q + 4]; else return su[(sr + q) * bs + sc]; };
-    auto fyv = [&](int q) { if constexpr (PREFETCH) return wy[2][q + 4]; else return sv[(sr + q) * bs + sc]; };
-    const T dpdx = deriv_general<T>(fxp, gx, d.nx, d.per_x, inv_h);
-    const T dpdy = deriv_general<T>(fyp, gy, d.ny, d.per_y, inv_h);
-    const T dudx = deriv_general<T>(fxu, gx, d.nx, d.per_x, inv_h);
-    const T dudy = deriv_general<T>(fyu, gy, d.ny, d.per_y, inv_h);
-    const T dvdx = deriv_general<T>(fxv, gx, d.nx, d.per_x, inv_h);
-    const T dvdy = deriv_general<T>(fyv, gy, d.ny, d.per_y, inv_h);
+    const T dpdx = band_deriv<T>(wx[0], tx, inv_h), dpdy = band_deriv<T>(wy[0], ty, inv_h);
+    const T dudx = band_deriv<T>(wx[1], tx, inv_h), dudy = band_deriv<T>(wy[1], ty, inv_h);
+    const T dvdx = band_deriv<T>(wx[2], tx, inv_h), dvdy = band_deriv<T>(wy[2], ty, inv_h);
     const T rx = T(gx) - (T)d.cx, ryy = T(gy) - (T)d.cy;
     T ct, st, q2;                                                // cos th, sin th, 1 / (2 h rho)
     if constexpr (sizeof(T) == 4) {
@@ -418,11 +455,11 @@ __device__ __forceinline__ void band_point(const T *sp, const T *su, const T *sv
         ct = rx / rho; st = ryy / rho; q2 = half_inv_h / rho;
     }
     const T sg = sk_h * ramp2<T>(d, gx, gy);
-    const T p0 = fxp(0), u0 = fxu(0), v0 = fxv(0);
+    const T p0 = wx[0][tx], u0 = wx[1][tx], v0 = wx[2][tx];
     const T rp = -(ct * dpdx + st * dpdy + p0 * q2) - sg * p0;
     const T ru = -(ct * dudx + st * dudy + u0 * q2) - sg * u0;
     const T rv = -(ct * dvdx + st * dvdy + v0 * q2) - sg * v0;
-    const long long o = (long long)gy * d.pitch + gx, plane = d.plane;
+    const long long o = (long long)gy * pitch + gx;
     const long long oq = qn.at(qx, qy);
     out[o] = qn.p[oq] + ad * rp;
     out[plane + o] = qn.u[oq] + ad * ru;
@@ -452,7 +489,7 @@ __device__ __forceinline__ void band_point(const T *sp, const T *su, const T *sv
 template <typename T, int RY, int FL, bool QNG, bool SKIPBAND = false>
 __device__ __forceinline__ void tile_points(const T *sp, const T *su, const T *sv, const int bs, const QnSrc<T> &qn,
                                             const InstDesc &d, T *out, int xt, int yt, const T *K, T src, int txi,
-                                            int tyi, unsigned short *wl_idx, int *wl_n) {
+                                            int tyi, unsigned short *wl_idx, int *wl_n, const T *gin = nullptr) {
     constexpr bool MIXED = (FL & TILE_MIXED) != 0, BAND = (FL & TILE_BAND) != 0, SPONGE = (FL & TILE_SPONGE) != 0;
     constexpr bool FOLD = sizeof(T) == 4;
     const int cx0 = HALO + 4 * txi, ry0 = HALO + RY * tyi;     // box coordinates of the first output
@@ -646,7 +683,7 @@ __device__ __forceinline__ void tile_points(const T *sp, const T *su, const T *s
         const int n = *(volatile int *)wl_n;
         for (int i = threadIdx.x & 31; i < n; i += 32) {
             const int e = wl_idx[i], lx = e & 0xff, ly = e >> 8;
-            band_point<T>(sp, su, sv, bs, HALO + ly, HALO + lx, qn, lx, ly, d, out, xt + lx, yt + ly, K);
+            band_point<T>(gin, qn, lx, ly, d, out, xt + lx, yt + ly, K);
         }
         __syncwarp();
         if ((threadIdx.x & 31) == 0) *wl_n = 0;
@@ -662,12 +699,12 @@ template <typename T, int RY, bool QNG>
 __device__ __forceinline__ void tile_dispatch(uint32_t flags, const T *sp, const T *su, const T *sv, const int bs,
                                               const QnSrc<T> &qn, const InstDesc &d, T *out, int xt, int yt,
                                               const T *K, T src, int txi, int tyi, unsigned short *wl_idx,
-                                              int *wl_n) {
+                                              int *wl_n, const T *gin) {
     if (flags == 0)
         tile_points<T, RY, 0, QNG>(sp, su, sv, bs, qn, d, out, xt, yt, K, src, txi, tyi, wl_idx, wl_n);
     else
         tile_points<T, RY, TILE_BAND | TILE_MIXED | TILE_SPONGE, QNG>(sp, su, sv, bs, qn, d, out, xt, yt, K, src,
-                                                                      txi, tyi, wl_idx, wl_n);
+                                                                      txi, tyi, wl_idx, wl_n, gin);
 }
 
 // Warp-specialised kernel: band nodes are left to band_kernel, which runs
@@ -781,7 +818,7 @@ stencil_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__restri
             qn = QnSrc<T>{q0, q0 + plane, q0 + 2 * plane, pitch};
         }
         tile_dispatch<T, RY, true>(flags, sp, su, sv, BOX_X, qn, d, out, xt, yt, stage_k<T>(d, stage), s_src, txi,
-                                   tyi, wl.idx[wid], &wl.n[wid]);
+                                   tyi, wl.idx[wid], &wl.n[wid], qin);
         __syncthreads();
     }
 }
@@ -843,6 +880,13 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const void *map, uint64_t
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::
             "r"(smem_u32(dst)), "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
         : "memory");
+}
+
+// a bounded wait gave up: flag every instance this block works on
+__device__ __noinline__ void flag_block_timeout(const InstDesc *__restrict__ inst, const int4 *__restrict__ strips,
+                                                int nstrips) {
+    for (int s2 = blockIdx.x; s2 < nstrips; s2 += gridDim.x)
+        atomicOr((unsigned long long *)&inst[__ldg(strips + s2).x].clock[2], STATUS_TIMEOUT);
 }
 
 template <int TW, int TH, int RYT>
@@ -915,15 +959,16 @@ stencil_tma_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ s
             float *out = (float *)d.q[outb];
             tile_dispatch<float, RYT, true>((uint32_t)inf.w, sp, su, sv, BW, qn, d, out, inf.y, inf.z,
                                             stage_k<float>(d, stage), ssrc[b], txi, tyi, wl.idx[tid >> 5],
-                                            &wl.n[tid >> 5]);
+                                            &wl.n[tid >> 5], (const float *)d.q[inb]);
         }
         __syncthreads();                               // every thread is done with stage b
         if (abort_flag) {
-            // a copy did not complete in time: flag the instance, let the copies
-            // still in flight land, and leave
+            // a copy did not complete in time: flag every instance of the block,
+            // let each copy issued so far land (tile k's, which timed out, and
+            // the ones ahead of it), and leave
             if (tid == 0) {
-                atomicOr((unsigned long long *)&inst[inf.x].clock[2], STATUS_TIMEOUT);
-                for (int q = 1; q < TMA_STAGES && k + q < ntiles; ++q)
+                flag_block_timeout(inst, strips, nstrips);
+                for (int q = 0; q < TMA_STAGES && k + q < ntiles; ++q)
                     mbar_wait_bounded(&bar[(k + q) % TMA_STAGES], ((k + q) / TMA_STAGES) & 1);
             }
             return;
@@ -962,13 +1007,6 @@ template <int TW, int TH, int RYT, int S_> struct WsGeom {
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// a bounded wait gave up: flag every instance this block works on
-__device__ __noinline__ void flag_block_timeout(const InstDesc *__restrict__ inst, const int4 *__restrict__ strips,
-                                                int nstrips) {
-    for (int s2 = blockIdx.x; s2 < nstrips; s2 += gridDim.x)
-        atomicOr((unsigned long long *)&inst[__ldg(strips + s2).x].clock[2], STATUS_TIMEOUT);
 }
 
 template <int TW, int TH, int RYT, int S_>
@@ -1115,8 +1153,7 @@ band_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ chunks, 
         const T *Q0 = (const T *)d.q[0];
         const long long plane = d.plane;
         const QnSrc<T> qn{Q0, Q0 + plane, Q0 + 2 * plane, d.pitch};
-        band_point<T, true>(P, P + plane, P + 2 * plane, d.pitch, gy, gx, qn, gx, gy, d, (T *)d.q[outb], gx, gy,
-                            stage_k<T>(d, stage));
+        band_point<T>(P, qn, gx, gy, d, (T *)d.q[outb], gx, gy, stage_k<T>(d, stage));
     }
 }
 

@@ -49,11 +49,11 @@ struct Setup {
 inline int wrapi(int i, int n) { i %= n; return i < 0 ? i + n : i; }
 
 // Axis footprint [lo, hi] of the derivative at index i: the 7-point DRP in the
-// interior (and on periodic axes), the 5-point stencils on nodes 0..4 /
-// n-5..n-1 in the three outer layers.
+// interior (and on periodic axes), the one-sided 7-point DRP stencils on nodes
+// 0..6 / n-7..n-1 in the three outer layers.
 inline void axis_footprint(int i, int n, int per, int &lo, int &hi) {
-    if (!per && i <= 2) { lo = 0; hi = 4; }
-    else if (!per && i >= n - 3) { lo = n - 5; hi = n - 1; }
+    if (!per && i <= 2) { lo = 0; hi = 6; }
+    else if (!per && i >= n - 3) { lo = n - 7; hi = n - 1; }
     else { lo = i - 3; hi = i + 3; }
 }
 
@@ -184,13 +184,13 @@ std::complex<double> rk4_poly(std::complex<double> z) {
 
 }  // namespace
 
-void fill_stage_constants(double dt, double h, float kf[4][8], double kd[4][8]) {
+void fill_stage_constants(double dt, double h, double kappa, float kf[4][8], double kd[4][8]) {
     static const double alpha[4] = {0.25, 1.0 / 3.0, 0.5, 1.0};       // 2N-storage Jameson scheme
     static const double a[3] = {0.770882380518, -0.166705904415, 0.020843142770};  // DRP, Sec. 2.2
     const double inv_h = 1.0 / h;
     for (int k = 0; k < 4; ++k) {
         const double ad = alpha[k] * dt, adh = ad * inv_h;
-        double v[8] = {ad, adh * a[0], adh * a[1], adh * a[2], adh * SPONGE_K, inv_h, SPONGE_K * inv_h, 0.0};
+        double v[8] = {ad, adh * a[0], adh * a[1], adh * a[2], adh * kappa, inv_h, kappa * inv_h, 0.0};
         for (int i = 0; i < 8; ++i) {
             kd[k][i] = v[i];
             kf[k][i] = (float)v[i];
@@ -224,7 +224,7 @@ void stage_forcing_factors(double omega, double dt, double G_re[4], double G_im[
 }
 
 int build_plan(int nx, int ny, double h, double x0, double y0, int per_x, int per_y, double dt, int tile_w, int tile_h,
-               const Geometry &geo, const Impedance &imp, const std::vector<double> &probe_xy,
+               int sponge_w, const Geometry &geo, const Impedance &imp, const std::vector<double> &probe_xy,
                Plan &P, std::string &err) {
     Setup S{nx, ny, per_x, per_y, h, x0, y0, geo};
     P = Plan();
@@ -295,14 +295,13 @@ int build_plan(int nx, int ny, double h, double x0, double y0, int per_x, int pe
                 const double ddx = S.xi(ii) - bpx, ddy = S.yj(jj) - bpy;
                 const double xr = (nrx * ddx + nry * ddy) / h;
                 const double yr = (-nry * ddx + nrx * ddy) / h;
-                if ((xr * xr) / 64.0 + (yr * yr) / 9.0 <= 1.0) {
+                if ((xr * xr) / (RN * RN) + (yr * yr) / (RT * RT) <= 1.0) {
                     if (N == MAXCLOUD) { G.status = LEE_ERR_GEOMETRY; break; }
                     G.idx.push_back(s); xp[N] = xr; yp[N] = yr; ++N;
                 }
             }
         }
         if (G.status) continue;
-        (void)RN; (void)RT;
         std::vector<xr> L((size_t)(KMAX + 1) * (N > 0 ? N : 1));
         int m = KMAX;
         while (m >= 1 && !readout_rows(N, xp, yp, m, L.data())) --m;
@@ -436,7 +435,8 @@ int build_plan(int nx, int ny, double h, double x0, double y0, int per_x, int pe
             if (!per_x && (xa < 3 || xb > nx - 3)) f |= TILE_BAND;
             if (!per_y && (ya < 3 || yb > ny - 3)) f |= TILE_BAND;
             if (per_x || per_y) f |= TILE_BAND;        // wrapped halos take the general path
-            if ((!per_x && (xa < SPONGE_W || xb > nx - SPONGE_W)) || (!per_y && (ya < SPONGE_W || yb > ny - SPONGE_W)))
+            if (sponge_w > 0 &&
+                ((!per_x && (xa < sponge_w || xb > nx - sponge_w)) || (!per_y && (ya < sponge_w || yb > ny - sponge_w))))
                 f |= TILE_SPONGE;
             if (xb > nx || yb > ny) f |= TILE_MIXED;
             for (int j = ya; j < std::min(yb, ny) && !(f & TILE_MIXED); ++j)

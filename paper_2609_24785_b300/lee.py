@@ -59,6 +59,8 @@ SIGNATURES = {
     "lee_set_impedance": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double]),
     "lee_set_rigid": (C.c_int, [_vp]),
     "lee_set_tile": (C.c_int, [_vp, C.c_int, C.c_int]),
+    "lee_set_sponge": (C.c_int, [_vp, C.c_int, C.c_double]),
+    "lee_fill_ghosts_with_bc": (C.c_int, [_vp, _dp]),
     "lee_plan": (C.c_int, [_vp, C.POINTER(lee_sizes)]),
     "lee_bind": (C.c_int, [_vp, _vp, C.c_longlong, _vp]),
     "lee_init_pulse": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double, C.c_double]),
@@ -186,6 +188,11 @@ class Solver:
         self._c(self.L.lee_set_probes(self.ctx, self._nprobe, _d(xy), int(capacity)))
         return self
 
+    def set_sponge(self, width, kappa=0.04):
+        """Opt-in absorbing ramp over `width` outer layers (0 = off, the default;
+        before plan); a departure from the paper, which adds no damping."""
+        self._c(self.L.lee_set_sponge(self.ctx, int(width), float(kappa))); return self
+
     def set_tile(self, tile_w, tile_h):
         """FP32 TMA stencil tile shape (before plan); (0, 0) = default."""
         self._c(self.L.lee_set_tile(self.ctx, int(tile_w), int(tile_h))); return self
@@ -273,6 +280,12 @@ class Solver:
     def write_state(self, blob):
         blob = np.ascontiguousarray(blob, dtype=np.uint8)
         self._c(self.L.lee_write_state(self.ctx, blob.ctypes.data_as(_vp)))
+
+    def fill_ghosts_with_bc(self, bc):
+        """Test hook: ghost nodes of Q^n from given boundary data, bc[g] =
+        (u.n, dp/dn) at ghost g's boundary point (steps 4-5 of Sec. 3.2)."""
+        a = np.ascontiguousarray(bc, dtype=np.float64).reshape(-1)
+        self._c(self.L.lee_fill_ghosts_with_bc(self.ctx, _d(a)))
 
     # ---- plan export (host; no device needed)
     def ghost(self, g):

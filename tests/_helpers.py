@@ -5,6 +5,15 @@ import oracle
 from paper_2609_24785_b300 import lee, workloads
 
 
+# one line per measured parity result, printed in pytest's terminal summary
+PARITY_LOG = []
+
+
+def log_result(line):
+    PARITY_LOG.append(line)
+    print(line)
+
+
 def make_solver(case, precision="fp64", bind=True, probe_capacity=None, tile=None):
     s = lee.Solver(case.nx, case.ny, case.h, case.cfl, precision=precision,
                    periodic_x=case.periodic[0], periodic_y=case.periodic[1])

@@ -18,7 +18,7 @@ import numpy as np
 import pytest
 
 from paper_2609_24785_b300 import lee, workloads
-from _helpers import make_oracle, make_solver, field_error, rel_l2
+from _helpers import make_oracle, make_solver, field_error, rel_l2, log_result
 
 pytestmark = pytest.mark.gpu
 
@@ -43,7 +43,8 @@ _ORACLE_RUNS = {}
 def run_oracle(case, steps, samples=10, f32_storage=False):
     """Oracle run; returns it with the largest field and ADE-state norms seen
     (cached per case and step count: the FP64 and FP32 runs share it)."""
-    key = (case.name, repr(case.wall), repr(case.imp), repr(case.init), repr(case.source), steps, f32_storage)
+    key = (case.name, repr(case.wall), repr(case.imp), repr(case.init), repr(case.source), repr(case.sponge), steps,
+           f32_storage)
     if key in _ORACLE_RUNS:
         return _ORACLE_RUNS[key]
     o = make_oracle(case, f32_storage=f32_storage)
@@ -83,9 +84,9 @@ def _check(case, precision, steps=None, ade=True, probes=True):
         f32, _, _, _ = run_oracle(case, steps, f32_storage=True)
         floor = _errors(f32, o, fluid, qmax, xmax)
         tol = [max(TOL["fp32"], FP32_FLOOR_FACTOR * fl) for fl in floor]
-        print("%s fp32 storage floor: field %.3e ade %.3e probes %.3e" % ((case.name,) + floor))
-    print("%s %s: field %.3e (final-norm relative %.3e) ade %.3e probes %.3e" %
-          (case.name, precision, err, field_error(s, o), ea, ep))
+        log_result("%s fp32-storage floor (oracle): field %.3e ade %.3e probes %.3e" % ((case.name,) + floor))
+    log_result("%s %s %d steps%s: field %.3e (final-norm relative %.3e) ade %.3e probes %.3e" %
+               (case.name, precision, steps, " ramp" if case.sponge[0] else "", err, field_error(s, o), ea, ep))
     assert err <= tol[0], (case.name, precision, err, tol[0])
     if ade and o.n_ghost and case.imp[0] == "msd" and xmax > 0:
         assert ea <= tol[1], ("ade", ea, tol[1])
@@ -331,3 +332,60 @@ def test_autotuner_returns_a_measured_configuration(cuda_device):
     assert res.tile in ((128, 28), (64, 60)) and res.strips_per_sm in (1, 4)
     assert len(res.table) == 4 and all(r["ms"] > 0 for r in res.table)
     assert res.ns_per_node == min(r["ns_per_node"] for r in res.table)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("case_name", ["cylinder", "line"])
+def test_fill_ghosts_with_bc_reproduces_polynomials(precision, case_name, cuda_device):
+    """P1 through the product's own ghost kernel (lee_fill_ghosts_with_bc):
+    with a bivariate polynomial field of degree <= 4 at the fluid nodes and
+    its exact u.n and dp/dn at every boundary point, the ghost values of every
+    full-degree ghost (clouds not clipped by the domain edge) equal the
+    polynomial at the ghost node (Sec. 3.1: the reconstruction is exact up to
+    its order); in FP64 a degree-5 field is not reproduced (the check
+    discriminates)."""
+    h = workloads.H
+    n = 96
+    c = ((n - 1) / 2 * h, (n - 1) / 2 * h)
+    if case_name == "cylinder":
+        case = workloads.Case("p1_cyl", n, n, wall=("cyl", c[0] + 0.3 * h, c[1] - 0.2 * h, 20.3 * h))
+    else:
+        case = workloads.Case("p1_line", n, n, wall=("line", c[0] + 0.37 * h, c[1], math.radians(23.0)))
+    s = make_solver(case, precision)
+    X, Y = np.meshgrid(np.arange(n) * h - c[0], np.arange(n) * h - c[1])
+    full = [g for g in range(s.sizes.n_ghost) if s.ghost(g)["m"] == 4]
+    assert len(full) > 200
+
+    def fields(deg):
+        k5 = 300.0 if deg > 4 else 0.0
+        p = lambda x, y: 0.3 + x - 0.7 * y + 2 * x * y + (1.5 * x ** 2 * y ** 2 - x ** 3 * y) * 4 + k5 * (x ** 5 + y ** 5)
+        u = lambda x, y: 0.1 - y + x * x * 3 - (x ** 4 - 2 * y ** 3 * x) * 5
+        v = lambda x, y: -0.2 + x * y - y ** 4 * 6 + x ** 3 * 2
+        dpdx = lambda x, y: 1 + 2 * y + (3 * x * y ** 2 - 3 * x ** 2 * y) * 4 + 5 * k5 * x ** 4
+        dpdy = lambda x, y: -0.7 + 2 * x + (3 * x ** 2 * y - x ** 3) * 4 + 5 * k5 * y ** 4
+        return p, u, v, dpdx, dpdy
+
+    for deg in ((4, 5) if precision == "fp64" else (4,)):
+        p, u, v, dpdx, dpdy = fields(deg)
+        for f, fn in enumerate((p, u, v)):
+            s.write_field(f, fn(X, Y))
+        bc = np.empty((s.sizes.n_ghost, 2))
+        targets = np.empty(s.sizes.n_ghost, dtype=np.int64)
+        for g in range(s.sizes.n_ghost):
+            gi = s.ghost(g)
+            bx, by = gi["bp"][0] - c[0], gi["bp"][1] - c[1]
+            nx_, ny_ = gi["n"]
+            bc[g] = (nx_ * u(bx, by) + ny_ * v(bx, by), nx_ * dpdx(bx, by) + ny_ * dpdy(bx, by))
+            targets[g] = gi["target"]
+        s.fill_ghosts_with_bc(bc)
+        err = 0.0
+        for f, fn in enumerate((p, u, v)):
+            got = s.field(f).reshape(-1)[targets[full]]
+            want = fn(X, Y).reshape(-1)[targets[full]]
+            err = max(err, float(np.abs(got - want).max()))
+        log_result("P1 %s %s degree %d: largest ghost error %.3e over %d full-degree ghosts" %
+                   (case_name, precision, deg, err, len(full)))
+        if deg == 4:
+            assert err < (1e-10 if precision == "fp64" else 2e-5), (deg, err)
+        else:
+            assert err > 1e-6, (deg, err)

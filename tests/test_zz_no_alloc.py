@@ -44,6 +44,38 @@ def test_energy_noalloc_matches_context_energy(precision, cuda_device):
     assert abs(results[0] - ref) <= TOL[precision] * ref, (results[0], ref)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_energy_noalloc_skips_pitch_padding(precision, cuda_device):
+    """Rows of `pitch` > nx elements: the padding columns (mask value 1 and
+    large field values there) must not enter the sum."""
+    import torch
+    case = workloads.cylinder_pulse(256, nx=250, ny=190)
+    s = make_solver(case, precision)
+    s.step(40)
+    s.sync()
+    ref = s.energy()
+    pitch = case.nx + 5
+    dt = torch.float64 if precision == "fp64" else torch.float32
+
+    def padded(a, fill):
+        b = np.full((case.ny, pitch), fill, dtype=a.dtype)
+        b[:, :case.nx] = a
+        return b
+    p, u, v = (torch.from_numpy(padded(s.field(f), 1e6)).to(dt).to(cuda_device) for f in range(3))
+    mask = torch.from_numpy(padded(np.ascontiguousarray(s.mask()), 1)).to(cuda_device)
+    out = torch.full((1,), -1.0, dtype=torch.float64, device=cuda_device)
+    L = lee.load()
+    stream = torch.cuda.current_stream(cuda_device)
+    prec = lee.LEE_FP64 if precision == "fp64" else lee.LEE_FP32
+    for _ in range(2):
+        rc = L.lee_energy_noalloc(C.c_void_p(p.data_ptr()), C.c_void_p(u.data_ptr()), C.c_void_p(v.data_ptr()),
+                                  C.c_void_p(mask.data_ptr()), case.nx, case.ny, pitch, prec, case.h,
+                                  C.c_void_p(out.data_ptr()), C.c_void_p(stream.cuda_stream))
+        assert rc == lee.LEE_OK, L.lee_last_error(None)
+        torch.cuda.synchronize()
+        assert abs(out.item() - ref) <= TOL[precision] * ref, (out.item(), ref)
+
+
 def test_energy_noalloc_rejects_rows_beyond_scratch(cuda_device):
     import torch
     L = lee.load()
