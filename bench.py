@@ -59,9 +59,13 @@ def parse():
     ap.add_argument("--tile", default=None, help="TMA tile WxH (skips the autotuner)")
     ap.add_argument("--strips", type=int, default=0, help="tile strips per SM with --tile (0: library default)")
     ap.add_argument("--serve-rate", type=float, default=200.0)
-    ap.add_argument("--serve-duration", type=float, default=0.05,
-                    help="seconds of Poisson arrivals of the serving trace")
-    ap.add_argument("--serve-fp64", type=int, default=1, help="also serve the trace per solve in FP64")
+    ap.add_argument("--serve-duration", type=float, default=1.0,
+                    help="seconds of Poisson arrivals of the saturated serving trace")
+    ap.add_argument("--serve-fp64", type=int, default=16,
+                    help="serve the first N requests of the trace per solve in FP64 as well (0: skip)")
+    ap.add_argument("--sustained-rate", type=float, default=3.0,
+                    help="arrival rate of the sustainable serving trace (0: skip)")
+    ap.add_argument("--sustained-duration", type=float, default=30.0)
     return ap.parse_args()
 
 
@@ -160,6 +164,24 @@ def cpu_baseline(case, target_seconds=15.0):
             "sample": "%s (%d fluid nodes), %d steps, %.1f s" % (case.name, fluid, n, el)}
 
 
+def cpu_baseline_one_core(case_index, target_seconds=10.0):
+    """The same oracle on one host thread (a child process with
+    OMP_NUM_THREADS=1, so that the parent's OpenMP pool is untouched)."""
+    code = (
+        "import sys, json; sys.path.insert(0, %r)\n"
+        "import bench\n"
+        "from paper_2609_24785_b300 import workloads\n"
+        "cases, _ = workloads.sweep(512, seed=24785)\n"
+        "print(json.dumps(bench.cpu_baseline(cases[%d], %r)))\n" % (ROOT, case_index, target_seconds))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                             timeout=10 * target_seconds + 60)
+        return json.loads(out.stdout.strip().splitlines()[-1])
+    except (subprocess.SubprocessError, ValueError, IndexError) as e:
+        return {"error": str(e)[:200]}
+
+
 def run_reference(args):
     ws, rank, local = dist_setup(args)
     if rank != 0:
@@ -204,19 +226,33 @@ def run_serving(args):
         except lee.LeeError:
             rejected[0] += 1
             return False
+    def describe(trace, rate, duration, redrawn):
+        sizes = sorted({c.nx for _, c in trace})
+        flat = sum(1 for _, c in trace if c.wall[0] == "line")
+        return ("Poisson %.0f/s for %.3f s (seed 24786): %d requests (%d flat walls, %d cylinders), n in %s, "
+                "%d-%d steps, %d draws redrawn (set-up rejected: unstable ADE), absorbing ramp %s" %
+                (rate, duration, len(trace), flat, len(trace) - flat, sizes, min(c.steps for _, c in trace),
+                 max(c.steps for _, c in trace), redrawn, trace[0][1].sponge))
     trace = workloads.serving_trace(rate=args.serve_rate, duration=args.serve_duration, accept=accept)
-    sizes = sorted({c.nx for _, c in trace})
-    out = {"trace": "Poisson %.0f/s for %.3f s (seed 24786): %d requests, n in %s, %d-%d steps, "
-                    "%d draws redrawn (set-up rejected: unstable ADE)" %
-                    (args.serve_rate, args.serve_duration, len(trace), sizes,
-                     min(c.steps for _, c in trace), max(c.steps for _, c in trace), rejected[0]),
+    out = {"trace": describe(trace, args.serve_rate, args.serve_duration, rejected[0]),
            "budget_bytes": 80 * 10**9}
     rep = serve.Server(serve.LeeBackend("fp32"), budget_bytes=80 * 10**9).run(trace, realtime=True)
     out["fp32_batched"] = rep.summary()
     if args.serve_fp64:
+        sub = trace[:args.serve_fp64]
+        rep32 = serve.Server(serve.LeeBackend("fp32"), budget_bytes=80 * 10**9).run(sub, realtime=True)
         rep64 = serve.Server(serve.LeeBackend("fp64", batching=False), max_slots=1,
-                             budget_bytes=80 * 10**9).run(trace, realtime=True)
-        out["fp64_per_solve"] = rep64.summary()
+                             budget_bytes=80 * 10**9).run(sub, realtime=True)
+        out["subset"] = "first %d requests of the trace, served alone in both modes" % len(sub)
+        out["subset_fp32_batched"] = rep32.summary()
+        out["subset_fp64_per_solve"] = rep64.summary()
+    if args.sustained_rate > 0:
+        rejected[0] = 0
+        tr = workloads.serving_trace(rate=args.sustained_rate, duration=args.sustained_duration, seed=24787,
+                                     accept=accept)
+        rep = serve.Server(serve.LeeBackend("fp32"), budget_bytes=80 * 10**9).run(tr, realtime=True)
+        out["sustained_trace"] = describe(tr, args.sustained_rate, args.sustained_duration, rejected[0])
+        out["sustained_fp32_batched"] = rep.summary()
     return out
 
 
@@ -359,6 +395,31 @@ def run_lee(args):
         except (ValueError, OSError):
             traffic = None
 
+    # ---- FP64: the stencil is bound by the FP64 pipe, not by HBM.  Its rate of
+    # FP64 instructions (32 per interior point-stage: four DRP derivatives of 7,
+    # the divergence, three stage FMAs) against this GPU's FP64 FMA rate,
+    # measured by a kernel of independent FMA chains on the same stream.
+    roofline_fp64 = None
+    if args.precision == "fp64":
+        sink = torch.zeros(1, dtype=torch.float64, device=dev)
+        L = lee.load()
+        blocks, iters = 148 * 8, 20000
+        for _ in range(2):
+            lee._check(L.lee_fp64_fma_probe(blocks, iters, sink.data_ptr(), stream.cuda_stream))
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(5):
+            lee._check(L.lee_fp64_fma_probe(blocks, iters, sink.data_ptr(), stream.cuda_stream))
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fma_s = f0.elapsed_time(f1) / 5 / 1e3
+        peak_instr = blocks * 256 * 8 * iters / fma_s / 1e9          # G FP64 FMA instructions / s
+        instr = 32.0 * fluid / (st_ms / 1e3) / 1e9
+        roofline_fp64 = {"bound": "alu", "achieved": instr, "peak": peak_instr, "unit": "G FP64 instr/s",
+                         "frac": instr / peak_instr, "peak_kind": "measured (FP64 FMA probe kernel, this run)",
+                         "peak_tflops": 2 * peak_instr / 1e3, "instr_per_point_stage": 32,
+                         "kernel": kname, "launch_ms": st_ms}
+
     # ---- end to end through the C ABI with host buffers: every step uploads
     # every instance's state from pinned host memory, advances one step and
     # reads back the step's probe record
@@ -402,6 +463,8 @@ def run_lee(args):
     if rank == 0 and not args.no_cpu:
         small = min(cases, key=lambda c: c.points)
         cpu = cpu_baseline(small)
+        if args.workload == "sweep" and args.count == 512 and rank == 0:
+            cpu["one_core"] = cpu_baseline_one_core(cases.index(small))
 
     if rank == 0:
         line = {
@@ -417,6 +480,7 @@ def run_lee(args):
                        (sum(s.sizes.device_bytes for s in solvers) / 1e9),
                        "parallelism": "replicas" if ws > 1 else "single GPU", "setup_s": round(t_setup, 2),
                        "stencil_kernel": batch.stencil_kernel(), "autotune": tuned},
+            "roofline_fp64": roofline_fp64,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": kname,

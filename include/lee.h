@@ -74,10 +74,12 @@ typedef struct {
     int n_fluid;              /* fluid nodes advanced per stage                          */
     long long n_entries;      /* total cloud entries over all ghosts                     */
     int n_reduced;            /* ghosts whose LSQ degree was lowered below k = 4         */
-    int regime;               /* 0 rigid, 1 complex pair, 2 real poles, 3 double pole    */
+    int regime;               /* 0 rigid, 1 complex pair, 2 real poles, 3 double pole,
+                                 4 rational admittance                                   */
     double dt;                /* time step                                               */
     double ade_amplification; /* max |P(pole dt)| of the RK4 polynomial over the poles  */
     int n_tiles;              /* stencil tiles                                           */
+    int n_states;             /* ADE states per ghost: 2 (MSD or rigid wall), N + 2M     */
 } lee_sizes;
 
 /* ---- context life cycle ------------------------------------------------- */
@@ -104,6 +106,21 @@ int lee_set_wall_cylinder(lee_ctx *ctx, double xc, double yc, double r);
 int lee_set_impedance(lee_ctx *ctx, double R, double M, double K);
 /* Rigid wall, the limit Y -> 0: u_n = 0 and dp/dn = 0 (Sec. 2.4). */
 int lee_set_rigid(lee_ctx *ctx);
+/* Broadband wall: the rational admittance of Sec. 2.3 (Eq. Yrational)
+ *   Y(s) = sum_k A_k / (s - lam_k) + sum_k [q_k / (s - s_k) + conj(q_k) / (s - conj(s_k))],
+ * s_k = alpha_k + i beta_k, q_k = B_k + i C_k, advanced by one real state per
+ * real pole and two per pair (Eq. ADEgeneral), u_n by Eq. unGeneral.
+ *   real   n_real x 2 doubles (lam_k < 0, A_k), host, copied;
+ *   pairs  n_pairs x 4 doubles (alpha_k < 0, beta_k > 0, B_k, C_k), host, copied.
+ * 1 <= n_real + 2 n_pairs <= 8.  The direct term Y_inf of Eq. Yrational is
+ * not supported: with Y_inf != 0 the Neumann datum du_n/dt of Sec. 3.2 step 4
+ * needs dp/dt at the boundary point, which the coupling does not provide.
+ * The RK4 stability check of lee_plan covers every pole.  LEE_ERR_ARG for
+ * counts out of range, a pole off the left half-plane or a non-finite
+ * residue.  Before lee_plan.  A batch that holds such an instance runs the
+ * general ADE for all its members (two-state walls then agree with their solo
+ * runs to rounding instead of bitwise). */
+int lee_set_impedance_rational(lee_ctx *ctx, int n_real, const double *real, int n_pairs, const double *pairs);
 /* Outer boundary of a non-periodic axis (Secs. 2.2, 4.1, 4.2): the three outer
  * layers use the one-sided 7-point DRP stencils of Tam and Webb (1993) and
  * their radiation condition dq/dt = -(cos th dq/dx + sin th dq/dy + q/(2 rho)),
@@ -181,7 +198,7 @@ int lee_sync(lee_ctx *ctx);
 int lee_read_field(lee_ctx *ctx, int which, double *host);
 /* Node kinds, nx*ny bytes: 0 solid, 1 fluid, 2 ghost. */
 int lee_read_mask(lee_ctx *ctx, unsigned char *host);
-/* ADE states X^n, n_ghost x 2 doubles, in the ghost order of lee_ghost_info. */
+/* ADE states X^n, n_ghost x n_states doubles, in the ghost order of lee_ghost_info. */
 int lee_read_ade(lee_ctx *ctx, double *host);
 /* Completed time steps. */
 int lee_get_step(lee_ctx *ctx, long long *steps);
@@ -284,6 +301,17 @@ int lee_batch_launch(lee_batch *b, int stage, int what);
  * calls on the same data give bitwise the same result. */
 int lee_energy_noalloc(const void *p, const void *u, const void *v, const unsigned char *mask, int nx, int ny,
                        long long pitch, int precision, double h, double *out, void *stream);
+
+/* ---- measurement ----------------------------------------------------------- */
+/* Enqueue on `stream` (cudaStream_t as void*, NULL = legacy default stream) a
+ * kernel of `blocks` x 256 threads that issues only FP64 fused multiply-adds:
+ * 8 independent chains of `iters` FMAs per thread, i.e. blocks * 256 * 8 *
+ * iters FMAs (2 flops each).  `sink` is a device double written only if the
+ * arithmetic left its bounded range (never), so the work is not optimised
+ * away.  The caller times the launch (CUDA events) to measure the FP64 FMA
+ * rate, the bound of the FP64 stencil path.  A measurement utility: the paper
+ * has no counterpart.  LEE_ERR_ARG for blocks < 1, iters < 1 or sink NULL. */
+int lee_fp64_fma_probe(int blocks, long long iters, double *sink, void *stream);
 
 /* ---- library --------------------------------------------------------------- */
 /* Kernel launches enqueued by this process so far (all contexts and batches). */

@@ -6,4 +6,5 @@ C source (``lee_oracle.c``) is written from the paper and shares no code with
 the CUDA path.  ``build()`` compiles it with gcc (``-ffp-contract=off``,
 OpenMP).
 """
-from .oracle import Oracle, build, deriv_1d, ade_drive, ade_regime, ade_stability, stage_forcing, lib_path  # noqa: F401
+from .oracle import (Oracle, build, deriv_1d, ade_drive, ade_regime, ade_stability, stage_forcing, lib_path,  # noqa: F401
+                     rational_drive)

@@ -46,6 +46,7 @@
 #include <stdio.h>
 
 #define ORC_MAXCL 160
+#define ORC_MAXPOLE 8
 
 /* ---------------------------------------------------------------- types */
 typedef struct {
@@ -71,8 +72,14 @@ typedef struct {
     double wa, wb, wc;          /* line: point, angle / cylinder: centre, radius */
     int rigid;
     double R, M, K;
-    int regime;                 /* 0 rigid, 1 complex pair, 2 real poles, 3 double pole */
+    int regime;                 /* 0 rigid, 1 complex pair, 2 real poles, 3 double pole, 4 rational */
     double A[2][2], bv[2], cv[2];
+    /* general rational admittance (Eq. Yrational): N real poles lam_k with
+     * residues A_k, M complex pairs s_k = al_k + i be_k with q_k = B_k + i C_k */
+    int nreal, npair;
+    double lam[ORC_MAXPOLE], Ares[ORC_MAXPOLE];
+    double al[ORC_MAXPOLE], be[ORC_MAXPOLE], Bres[ORC_MAXPOLE], Cres[ORC_MAXPOLE];
+    int ns;                     /* ADE states per ghost: 2 (MSD, rigid) or N + 2M */
     double s_amp, s_x, s_y, s_b, s_omega;
     unsigned char *kind;        /* 0 solid, 1 fluid, 2 ghost */
     double *q[3];               /* Q^n: p, u, v */
@@ -171,9 +178,24 @@ void orc_set_line(orc_t *o, double xw, double yw, double angle)
 { o->wall = 1; o->wa = xw; o->wb = yw; o->wc = angle; }
 void orc_set_cylinder(orc_t *o, double xc, double yc, double rad)
 { o->wall = 2; o->wa = xc; o->wb = yc; o->wc = rad; }
-void orc_set_rigid(orc_t *o) { o->rigid = 1; }
+void orc_set_rigid(orc_t *o) { o->rigid = 1; o->nreal = o->npair = 0; }
 void orc_set_msd(orc_t *o, double R, double M, double K)
-{ o->rigid = 0; o->R = R; o->M = M; o->K = K; }
+{ o->rigid = 0; o->R = R; o->M = M; o->K = K; o->nreal = o->npair = 0; }
+
+/* General rational admittance of Eq. Yrational with Y_inf = 0: nreal real
+ * poles lam[k] < 0 with real residues A[k], npair complex-conjugate pairs
+ * s_k = al[k] + i be[k] (al < 0, be > 0) with residues q_k = B[k] + i C[k];
+ * nreal + 2 npair <= ORC_MAXPOLE states per ghost (Eq. ADEgeneral).
+ * Returns 0, or -1 for counts out of range. */
+int orc_set_rational(orc_t *o, int nreal, const double *lam, const double *A,
+                     int npair, const double *al, const double *be, const double *B, const double *C)
+{
+    if (nreal < 0 || npair < 0 || nreal + 2 * npair < 1 || nreal + 2 * npair > ORC_MAXPOLE) return -1;
+    o->rigid = 0; o->nreal = nreal; o->npair = npair;
+    for (int k = 0; k < nreal; k++) { o->lam[k] = lam[k]; o->Ares[k] = A[k]; }
+    for (int k = 0; k < npair; k++) { o->al[k] = al[k]; o->be[k] = be[k]; o->Bres[k] = B[k]; o->Cres[k] = C[k]; }
+    return 0;
+}
 void orc_set_monopole(orc_t *o, double xs, double ys, double amp, double w, double omega)
 {
     o->s_amp = amp; o->s_x = xs; o->s_y = ys; o->s_omega = omega;
@@ -504,6 +526,8 @@ int orc_setup(orc_t *o)
     orc_free_ghosts(o);
     o->err[0] = 0;
     orc_ade_coeffs(o->rigid, o->R, o->M, o->K, &o->regime, o->A, o->bv, o->cv);
+    o->ns = 2;
+    if (!o->rigid && o->nreal + o->npair > 0) { o->regime = 4; o->ns = o->nreal + 2 * o->npair; }
     /* mask: fluid / solid (Sec. 3.1) */
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++)
@@ -528,7 +552,7 @@ int orc_setup(orc_t *o)
     for (int s = 0; s < nx * ny; s++) ng += o->kind[s] == 2;
     o->ng = ng;
     o->g = (orc_ghost *)calloc(ng > 0 ? ng : 1, sizeof(orc_ghost));
-    o->X = (double *)calloc(2 * (ng > 0 ? ng : 1), sizeof(double));
+    o->X = (double *)calloc((size_t)o->ns * (ng > 0 ? ng : 1), sizeof(double));
     int *gs = (int *)malloc(sizeof(int) * (ng > 0 ? ng : 1));
     int c = 0;
     for (int s = 0; s < nx * ny; s++) if (o->kind[s] == 2) gs[c++] = s;
@@ -584,7 +608,7 @@ void orc_init_pulse(orc_t *o, double xs, double ys, double amp, double w)
             o->q[0][s] = o->kind[s] == 1 ? stored(o, amp * exp(-b * (dx * dx + dy * dy))) : 0.0;
             o->q[1][s] = 0.0; o->q[2][s] = 0.0;
         }
-    memset(o->X, 0, sizeof(double) * 2 * (o->ng > 0 ? o->ng : 1));
+    memset(o->X, 0, sizeof(double) * o->ns * (o->ng > 0 ? o->ng : 1));
     o->step = 0; o->prec = 0;
 }
 
@@ -601,7 +625,7 @@ void orc_init_packet(orc_t *o, double xs, double ys, double ang, double amp, dou
                      ? 0.5 * amp * exp(-alpha * alpha * s * s) * cos(2.0 * M_PI * k * s) : 0.0;
             o->q[0][sidx] = stored(o, p); o->q[1][sidx] = stored(o, p * ca); o->q[2][sidx] = stored(o, p * sa);
         }
-    memset(o->X, 0, sizeof(double) * 2 * (o->ng > 0 ? o->ng : 1));
+    memset(o->X, 0, sizeof(double) * o->ns * (o->ng > 0 ? o->ng : 1));
     o->step = 0; o->prec = 0;
 }
 
@@ -609,8 +633,9 @@ void orc_get_field(orc_t *o, int which, double *out)
 { memcpy(out, o->q[which], sizeof(double) * o->nx * o->ny); }
 void orc_set_field(orc_t *o, int which, const double *in)
 { memcpy(o->q[which], in, sizeof(double) * o->nx * o->ny); }
-void orc_get_ade(orc_t *o, double *out) { memcpy(out, o->X, sizeof(double) * 2 * o->ng); }
-void orc_set_ade(orc_t *o, const double *in) { memcpy(o->X, in, sizeof(double) * 2 * o->ng); }
+void orc_get_ade(orc_t *o, double *out) { memcpy(out, o->X, sizeof(double) * o->ns * o->ng); }
+void orc_set_ade(orc_t *o, const double *in) { memcpy(o->X, in, sizeof(double) * o->ns * o->ng); }
+int orc_n_states(orc_t *o) { return o->ns; }
 long orc_get_step(orc_t *o) { return o->step; }
 
 /* ------------------------------------------------------------ probes */
@@ -734,6 +759,42 @@ static int in_band(const orc_t *o, int i, int j)
 }
 
 /*
+ * Steps 2-3 of Sec. 3.2 for one ghost: the ADE derivative xd of the states x
+ * forced by p_BP, the wall normal velocity u_n and its time derivative.
+ * MSD wall (Sec. 2.5): the 2 x 2 form of its regime.  Rational admittance:
+ * Eq. ADEgeneral state by state (real poles first, then the pairs) and
+ * Eq. unGeneral with Y_inf = 0.
+ */
+static void ade_eval(const orc_t *o, const double *x, double pbp, double *xd, double *un, double *dun)
+{
+    if (o->regime != 4) {
+        xd[0] = o->A[0][0] * x[0] + o->A[0][1] * x[1] + o->bv[0] * pbp;
+        xd[1] = o->A[1][0] * x[0] + o->A[1][1] * x[1] + o->bv[1] * pbp;
+        *un = o->cv[0] * x[0] + o->cv[1] * x[1];
+        *dun = o->cv[0] * xd[0] + o->cv[1] * xd[1];
+        return;
+    }
+    double u = 0.0, du = 0.0;
+    for (int k = 0; k < o->nreal; k++) {
+        const double phi = x[k];
+        const double dphi = o->lam[k] * phi + pbp;                          /* Eq. ADEgeneral a */
+        xd[k] = dphi;
+        u += o->Ares[k] * phi;                                              /* Eq. unGeneral */
+        du += o->Ares[k] * dphi;
+    }
+    for (int k = 0; k < o->npair; k++) {
+        const double *psi = x + o->nreal + 2 * k;
+        double *dpsi = xd + o->nreal + 2 * k;
+        dpsi[0] = o->al[k] * psi[0] - o->be[k] * psi[1] + pbp;             /* Eq. ADEgeneral b */
+        dpsi[1] = o->al[k] * psi[1] + o->be[k] * psi[0];                   /* Eq. ADEgeneral c */
+        u += 2.0 * (o->Bres[k] * psi[0] - o->Cres[k] * psi[1]);
+        du += 2.0 * (o->Bres[k] * dpsi[0] - o->Cres[k] * dpsi[1]);
+    }
+    *un = u;
+    *dun = du;
+}
+
+/*
  * One evaluation of the semi-discrete right-hand side of Q = [p; u; v; X]
  * (Sec. 3.2).  Steps 1-5 fill the ghost nodes of q (in place) and give the
  * ADE derivative Xd; step 6 evaluates the DRP / radiation right-hand side at
@@ -763,14 +824,12 @@ static void orc_rhs(orc_t *o, double *q[3], const double *X, double sigma, doubl
         }
         /* 1: pressure at the boundary point */
         double pbp = Pp[0];
-        /* 2: ADE derivative at this stage */
-        const double *x = X + 2 * g;
-        double xd0 = o->A[0][0] * x[0] + o->A[0][1] * x[1] + o->bv[0] * pbp;
-        double xd1 = o->A[1][0] * x[0] + o->A[1][1] * x[1] + o->bv[1] * pbp;
-        Xd[2 * g] = xd0; Xd[2 * g + 1] = xd1;
-        /* 3: wall normal velocity and its time derivative */
-        double un = o->cv[0] * x[0] + o->cv[1] * x[1];
-        double dun = o->cv[0] * xd0 + o->cv[1] * xd1;
+        /* 2-3: ADE derivative at this stage, wall normal velocity and its
+         * time derivative */
+        const double *x = X + (size_t)o->ns * g;
+        double *xd = Xd + (size_t)o->ns * g;
+        double un, dun;
+        ade_eval(o, x, pbp, xd, &un, &dun);
         /* 4: boundary data: w_BP = -u_n (Dirichlet), dp/dn_BP = +du_n/dt (Neumann) */
         double gD = -un, gN = dun;
         if (o->bc_override) { gD = o->bc_override[2 * g]; gN = o->bc_override[2 * g + 1]; }
@@ -826,7 +885,8 @@ void orc_run(orc_t *o, long nsteps, int classical)
     const double dt = o->dt;
     /* work arrays: allocated on the first call and kept, so that repeated
      * short runs time the method and not the allocator */
-    size_t gx = 2 * (size_t)(ng > 0 ? ng : 1);
+    const size_t nsx = (size_t)o->ns * ng;       /* ADE states of all ghosts */
+    size_t gx = (size_t)o->ns * (ng > 0 ? ng : 1);
     size_t need = 9 * n + 3 * gx;
     if (o->work_n < need) {
         free(o->work);
@@ -847,7 +907,7 @@ void orc_run(orc_t *o, long nsteps, int classical)
         const double tn = (double)o->step * dt;
         if (!classical) {
             for (int f = 0; f < 3; f++) memcpy(qs[f], o->q[f], sizeof(double) * n);
-            memcpy(Xs, o->X, sizeof(double) * 2 * ng);
+            memcpy(Xs, o->X, sizeof(double) * nsx);
             for (int k = 0; k < 4; k++) {
                 orc_rhs(o, qs, Xs, stage_forcing(o->s_omega, tn, dt, k + 1), rq, Xd);
                 const double ad = alpha[k] * dt;
@@ -855,16 +915,16 @@ void orc_run(orc_t *o, long nsteps, int classical)
                 for (size_t s = 0; s < n; s++)
                     for (int f = 0; f < 3; f++)
                         qs[f][s] = o->kind[s] == 1 ? stored(o, o->q[f][s] + ad * rq[f][s]) : 0.0;
-                for (int g = 0; g < 2 * ng; g++) Xs[g] = o->X[g] + ad * Xd[g];
+                for (size_t g = 0; g < nsx; g++) Xs[g] = o->X[g] + ad * Xd[g];
             }
             for (int f = 0; f < 3; f++) memcpy(o->q[f], qs[f], sizeof(double) * n);
-            memcpy(o->X, Xs, sizeof(double) * 2 * ng);
+            memcpy(o->X, Xs, sizeof(double) * nsx);
         } else {
             static const double cw[4] = {1.0, 2.0, 2.0, 1.0};
             static const double cf[4] = {0.5, 0.5, 1.0, 0.0};
             static const double tc[4] = {0.0, 0.5, 0.5, 1.0};
             for (int f = 0; f < 3; f++) { memcpy(qs[f], o->q[f], sizeof(double) * n); memset(acc[f], 0, sizeof(double) * n); }
-            memcpy(Xs, o->X, sizeof(double) * 2 * ng);
+            memcpy(Xs, o->X, sizeof(double) * nsx);
             memset(Xacc, 0, sizeof(double) * gx);
             for (int k = 0; k < 4; k++) {
                 orc_rhs(o, qs, Xs, sin(o->s_omega * (tn + tc[k] * dt)), rq, Xd);
@@ -873,7 +933,7 @@ void orc_run(orc_t *o, long nsteps, int classical)
                         acc[f][s] += cw[k] * rq[f][s];
                         qs[f][s] = o->kind[s] == 1 ? o->q[f][s] + cf[k] * dt * rq[f][s] : 0.0;
                     }
-                for (int g = 0; g < 2 * ng; g++) {
+                for (size_t g = 0; g < nsx; g++) {
                     Xacc[g] += cw[k] * Xd[g];
                     Xs[g] = o->X[g] + cf[k] * dt * Xd[g];
                 }
@@ -881,7 +941,7 @@ void orc_run(orc_t *o, long nsteps, int classical)
             for (size_t s = 0; s < n; s++)
                 for (int f = 0; f < 3; f++)
                     o->q[f][s] = o->kind[s] == 1 ? o->q[f][s] + dt / 6.0 * acc[f][s] : 0.0;
-            for (int g = 0; g < 2 * ng; g++) o->X[g] += dt / 6.0 * Xacc[g];
+            for (size_t g = 0; g < nsx; g++) o->X[g] += dt / 6.0 * Xacc[g];
         }
         o->step++;
         record_probes(o);
@@ -895,9 +955,9 @@ void orc_fill_ghosts(orc_t *o, double *Xd_out)
     const size_t n = (size_t)o->nx * o->ny;
     double *rq[3];
     for (int f = 0; f < 3; f++) rq[f] = (double *)malloc(sizeof(double) * n);
-    double *Xd = (double *)malloc(sizeof(double) * 2 * (o->ng > 0 ? o->ng : 1));
+    double *Xd = (double *)malloc(sizeof(double) * o->ns * (o->ng > 0 ? o->ng : 1));
     orc_rhs(o, o->q, o->X, sin(o->s_omega * (double)o->step * o->dt), rq, Xd);
-    if (Xd_out) memcpy(Xd_out, Xd, sizeof(double) * 2 * o->ng);
+    if (Xd_out) memcpy(Xd_out, Xd, sizeof(double) * o->ns * o->ng);
     for (int f = 0; f < 3; f++) free(rq[f]);
     free(Xd);
 }
@@ -926,6 +986,36 @@ double orc_energy(orc_t *o)
     for (size_t s = 0; s < (size_t)o->nx * o->ny; s++)
         if (o->kind[s] == 1) e += o->q[0][s] * o->q[0][s] + o->q[1][s] * o->q[1][s] + o->q[2][s] * o->q[2][s];
     return 0.5 * o->h * o->h * e;
+}
+
+/*
+ * The rational-admittance ADE alone (Eqs. ADEgeneral, unGeneral), forced by
+ * p_BP(t) = sin(omega t) and advanced by the four stages with the same stage
+ * forcing moments as the source; returns u_n after each step.
+ * Pin: u_n equals the convolution of the kernel y(t) of Eq. Yrational's
+ * inverse Laplace transform with the forcing, up to O(dt^4).
+ */
+void orc_rational_drive(int nreal, const double *lam, const double *A, int npair, const double *al,
+                        const double *be, const double *B, const double *C, double dt, long nsteps,
+                        double omega, double *un_out)
+{
+    orc_t o;
+    memset(&o, 0, sizeof o);
+    orc_set_rational(&o, nreal, lam, A, npair, al, be, B, C);
+    o.regime = 4;
+    o.ns = nreal + 2 * npair;
+    static const double alpha[4] = {0.25, 1.0 / 3.0, 0.5, 1.0};
+    double X[ORC_MAXPOLE] = {0}, Xs[ORC_MAXPOLE], Xd[ORC_MAXPOLE], un, dun;
+    for (long n = 0; n < nsteps; n++) {
+        memcpy(Xs, X, sizeof X);
+        for (int k = 0; k < 4; k++) {
+            ade_eval(&o, Xs, stage_forcing(omega, (double)n * dt, dt, k + 1), Xd, &un, &dun);
+            for (int i = 0; i < o.ns; i++) Xs[i] = X[i] + alpha[k] * dt * Xd[i];
+        }
+        memcpy(X, Xs, sizeof X);
+        ade_eval(&o, X, 0.0, Xd, &un, &dun);
+        un_out[n] = un;
+    }
 }
 
 /*

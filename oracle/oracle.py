@@ -62,6 +62,10 @@ def _load():
             "orc_setup": (C.c_int, [vp]),
             "orc_set_f32_storage": (None, [vp, C.c_int]),
             "orc_set_sponge": (None, [vp, C.c_int, C.c_double]),
+            "orc_set_rational": (C.c_int, [vp, C.c_int, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp]),
+            "orc_n_states": (C.c_int, [vp]),
+            "orc_rational_drive": (None, [C.c_int, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp, C.c_double, C.c_long,
+                                          C.c_double, _dp]),
             "orc_n_ghost": (C.c_int, [vp]),
             "orc_n_reduced": (C.c_int, [vp]),
             "orc_regime": (C.c_int, [vp]),
@@ -120,6 +124,25 @@ def ade_drive(R, M, K, dt, nsteps, omega):
     return un, X
 
 
+def _poles(real, pairs):
+    """(n, lam, A, m, al, be, B, C) arrays from real = [(lam, A)], pairs =
+    [(alpha, beta, B, C)] (Eq. Yrational)."""
+    real = np.asarray(real, dtype=np.float64).reshape(-1, 2)
+    pairs = np.asarray(pairs, dtype=np.float64).reshape(-1, 4)
+    cols = [np.ascontiguousarray(real[:, i]) for i in range(2)] + [np.ascontiguousarray(pairs[:, i]) for i in range(4)]
+    cols = [c if c.size else np.zeros(1) for c in cols]
+    return len(real), cols[0], cols[1], len(pairs), cols[2], cols[3], cols[4], cols[5]
+
+
+def rational_drive(real, pairs, dt, nsteps, omega):
+    """Eqs. ADEgeneral/unGeneral alone forced by sin(omega t): u_n per step."""
+    L = _load()
+    n, lam, A, m, al, be, B, Cc = _poles(real, pairs)
+    un = np.empty(nsteps)
+    L.orc_rational_drive(n, _d(lam), _d(A), m, _d(al), _d(be), _d(B), _d(Cc), dt, nsteps, omega, _d(un))
+    return un
+
+
 def ade_regime(R, M, K):
     """Returns (regime, A (2x2), b, c): 1 complex pair, 2 real poles, 3 double pole."""
     L = _load()
@@ -175,6 +198,18 @@ class Oracle:
     def set_f32_storage(self, on=True):
         """Emulate FP32 storage of the field (tolerance studies only)."""
         self._L.orc_set_f32_storage(self._o, int(bool(on)))
+
+    def set_impedance_rational(self, real=(), pairs=()):
+        """Rational admittance of Eq. Yrational (Y_inf = 0): real = [(lam, A)],
+        pairs = [(alpha, beta, B, C)] for poles alpha +- i beta, residues B +- i C."""
+        n, lam, A, m, al, be, B, Cc = _poles(real, pairs)
+        rc = self._L.orc_set_rational(self._o, n, _d(lam), _d(A), m, _d(al), _d(be), _d(B), _d(Cc))
+        if rc:
+            raise ValueError("rational admittance: 1..8 states")
+
+    @property
+    def n_states(self):
+        return self._L.orc_n_states(self._o)
 
     def set_sponge(self, width, kappa=0.04):
         """Opt-in absorbing ramp over `width` outer layers (0 = off, the default);
@@ -243,9 +278,10 @@ class Oracle:
         self._L.orc_set_field(self._o, which, _d(a))
 
     def ade(self):
-        out = np.empty(2 * max(self.n_ghost, 1))
+        ns = self.n_states
+        out = np.empty(ns * max(self.n_ghost, 1))
         self._L.orc_get_ade(self._o, _d(out))
-        return out[:2 * self.n_ghost].reshape(-1, 2)
+        return out[:ns * self.n_ghost].reshape(-1, ns)
 
     def set_ade(self, X):
         a = np.ascontiguousarray(X, dtype=np.float64).reshape(-1)
@@ -268,9 +304,10 @@ class Oracle:
         self._L.orc_run(self._o, nsteps, int(classical))
 
     def fill_ghosts(self):
-        Xd = np.empty(2 * max(self.n_ghost, 1))
+        ns = self.n_states
+        Xd = np.empty(ns * max(self.n_ghost, 1))
         self._L.orc_fill_ghosts(self._o, _d(Xd))
-        return Xd[:2 * self.n_ghost].reshape(-1, 2)
+        return Xd[:ns * self.n_ghost].reshape(-1, ns)
 
     def fill_ghosts_bc(self, bc):
         """Ghost fill from given (w_BP, dp/dn_BP) per ghost (steps 4-5 only)."""
@@ -280,10 +317,11 @@ class Oracle:
     def eval_rhs(self, t):
         n = self.nx * self.ny
         rp, ru, rv = np.empty(n), np.empty(n), np.empty(n)
-        Xd = np.empty(2 * max(self.n_ghost, 1))
+        ns = self.n_states
+        Xd = np.empty(ns * max(self.n_ghost, 1))
         self._L.orc_eval_rhs(self._o, t, _d(rp), _d(ru), _d(rv), _d(Xd))
         sh = (self.ny, self.nx)
-        return rp.reshape(sh), ru.reshape(sh), rv.reshape(sh), Xd[:2 * self.n_ghost].reshape(-1, 2)
+        return rp.reshape(sh), ru.reshape(sh), rv.reshape(sh), Xd[:ns * self.n_ghost].reshape(-1, ns)
 
     def energy(self):
         return self._L.orc_energy(self._o)

@@ -9,7 +9,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "liblee.so")
-SOURCES = ["lee_kernels.cu", "lee_setup.cpp", "lee_api.cpp", "lee_noalloc.cu"]
+SOURCES = ["lee_kernels.cu", "lee_setup.cpp", "lee_api.cpp", "lee_noalloc.cu", "lee_measure.cu"]
 HEADERS = ["lee_internal.h", os.path.join("..", "..", "include", "lee.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

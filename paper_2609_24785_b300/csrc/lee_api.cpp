@@ -25,7 +25,7 @@ constexpr int GRAPH_STEPS = 8;
 
 struct Layout {
     size_t q, mask, tiles, gt, gs, gn, gk, ei, ew, xn, xs, gx, gy, pi, pw, ph, clock, scratch, staging, desc,
-        prefix, chunks, strips, tmap, bchunks, bc, total;
+        prefix, chunks, strips, tmap, bchunks, bc, ade, total;
 };
 
 // TMA stencil work list of one instance: columns of tiles (instance, tile
@@ -148,8 +148,8 @@ Layout make_layout(const lee_ctx *c) {
     L.gk = take((size_t)ng * 16);
     L.ei = take(ne * 4);
     L.ew = take(ne * 32);
-    L.xn = take((size_t)ng * 16);
-    L.xs = take((size_t)ng * 16);
+    L.xn = take((size_t)ng * 8 * P.ns);
+    L.xs = take((size_t)ng * 8 * P.ns);
     L.gx = take((size_t)P.nx * c->elem());
     L.gy = take((size_t)P.ny * c->elem());
     L.pi = take((size_t)np * 16 * 4);
@@ -165,6 +165,7 @@ Layout make_layout(const lee_ctx *c) {
     L.tmap = take(4 * 128);
     L.bchunks = take(((size_t)ctx_band_nodes(c) / 64 + 2) * sizeof(int4));
     L.bc = take((size_t)ng * 16);
+    L.ade = take(P.ade_coef.size() * 8);
     L.total = o;
     return L;
 }
@@ -280,6 +281,7 @@ BatchView single_view(lee_ctx *c) {
     bv.total_tiles = c->hd.ntiles;
     bv.total_ghosts = c->hd.ng;
     bv.precision = c->g.precision;
+    bv.ade_general = c->hd.ns != 2;
     return bv;
 }
 
@@ -289,8 +291,8 @@ int reset_state(lee_ctx *ctx) {
     CK(cudaMemsetAsync(ctx->dev + ctx->L.q, 0, 9 * plane * ctx->elem(), ctx->stream));
     const int ng = (int)P.g_target.size();
     if (ng) {
-        CK(cudaMemsetAsync(ctx->dev + ctx->L.xn, 0, (size_t)ng * 16, ctx->stream));
-        CK(cudaMemsetAsync(ctx->dev + ctx->L.xs, 0, (size_t)ng * 16, ctx->stream));
+        CK(cudaMemsetAsync(ctx->dev + ctx->L.xn, 0, (size_t)ng * 8 * P.ns, ctx->stream));
+        CK(cudaMemsetAsync(ctx->dev + ctx->L.xs, 0, (size_t)ng * 8 * P.ns, ctx->stream));
     }
     static const long long clk[8] = {-1, 0, 0, 0, 0, 0, 0, 0};
     CK(cudaMemcpyAsync(ctx->dev + ctx->L.clock, clk, sizeof clk, cudaMemcpyHostToDevice, ctx->stream));
@@ -351,6 +353,32 @@ int lee_set_impedance(lee_ctx *ctx, double R, double M, double K) {
     if (!ctx || ctx->planned) return ctx ? fail(ctx, LEE_ERR_ARG, "impedance is fixed after lee_plan") : LEE_ERR_ARG;
     if (!(R > 0 && M > 0 && K > 0)) return fail(ctx, LEE_ERR_ARG, "impedance needs R, M, K > 0");
     ctx->imp = Impedance{false, R, M, K};
+    return LEE_OK;
+}
+int lee_set_impedance_rational(lee_ctx *ctx, int n_real, const double *real, int n_pairs, const double *pairs) {
+    if (!ctx || ctx->planned) return ctx ? fail(ctx, LEE_ERR_ARG, "impedance is fixed after lee_plan") : LEE_ERR_ARG;
+    if (n_real < 0 || n_pairs < 0 || n_real + 2 * n_pairs < 1 || n_real + 2 * n_pairs > MAX_ADE_STATES ||
+        (n_real && !real) || (n_pairs && !pairs))
+        return fail(ctx, LEE_ERR_ARG, "rational admittance needs 1..8 states (n_real + 2 n_pairs)");
+    Impedance imp;
+    imp.rigid = false;
+    imp.nreal = n_real;
+    imp.npair = n_pairs;
+    for (int k = 0; k < n_real; ++k) {
+        imp.lam[k] = real[2 * k];
+        imp.A[k] = real[2 * k + 1];
+        if (!(imp.lam[k] < 0) || !std::isfinite(imp.A[k]))
+            return fail(ctx, LEE_ERR_ARG, "rational admittance: real poles must be negative, residues finite");
+    }
+    for (int k = 0; k < n_pairs; ++k) {
+        imp.al[k] = pairs[4 * k];
+        imp.be[k] = pairs[4 * k + 1];
+        imp.B[k] = pairs[4 * k + 2];
+        imp.C[k] = pairs[4 * k + 3];
+        if (!(imp.al[k] < 0 && imp.be[k] > 0) || !std::isfinite(imp.B[k]) || !std::isfinite(imp.C[k]))
+            return fail(ctx, LEE_ERR_ARG, "rational admittance: pairs need alpha < 0 < beta, finite residues");
+    }
+    ctx->imp = imp;
     return LEE_OK;
 }
 int lee_set_rigid(lee_ctx *ctx) {
@@ -426,6 +454,7 @@ int lee_plan(lee_ctx *ctx, lee_sizes *out) {
     out->dt = g.cfl * g.h;
     out->ade_amplification = ctx->plan.ade_amp;
     out->n_tiles = ctx->plan.tiles_x * ctx->plan.tiles_y;
+    out->n_states = ctx->plan.ns;
     return LEE_OK;
 }
 
@@ -484,6 +513,8 @@ int lee_bind(lee_ctx *ctx, void *dev_ptr, long long dev_bytes, void *stream) {
         else
             CK(cudaMemcpyAsync(ctx->dev + L.ew, P.e_w.data(), P.e_w.size() * 8, cudaMemcpyHostToDevice, s));
     }
+    if (!P.ade_coef.empty())
+        CK(cudaMemcpyAsync(ctx->dev + L.ade, P.ade_coef.data(), P.ade_coef.size() * 8, cudaMemcpyHostToDevice, s));
     const int np = (int)ctx->probe_xy.size() / 2;
     if (np) {
         CK(cudaMemcpyAsync(ctx->dev + L.pi, pidx.data(), pidx.size() * 4, cudaMemcpyHostToDevice, s));
@@ -534,6 +565,8 @@ int lee_bind(lee_ctx *ctx, void *dev_ptr, long long dev_bytes, void *stream) {
     d.scratch = (double *)(ctx->dev + L.scratch);
     d.staging = (double *)(ctx->dev + L.staging);
     d.bc = (const double *)(ctx->dev + L.bc);
+    d.ade = (const double *)(ctx->dev + L.ade);
+    d.ns = P.ns;
     d.precision = ctx->g.precision;
     d.kernel_mode = ctx->kernel_mode;
     d.use_tma = ctx->kernel_mode == KERNEL_TMA;
@@ -644,7 +677,7 @@ int lee_read_ade(lee_ctx *ctx, double *host) {
     if (!ctx || !host) return LEE_ERR_ARG;
     if (!ctx->bound) return fail(ctx, LEE_ERR_ARG, "not bound");
     if (ctx->hd.ng == 0) return LEE_OK;
-    CK(cudaMemcpyAsync(host, ctx->hd.Xn, (size_t)ctx->hd.ng * 16, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(host, ctx->hd.Xn, (size_t)ctx->hd.ng * 8 * ctx->hd.ns, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return LEE_OK;
 }
@@ -689,7 +722,8 @@ int lee_energy(lee_ctx *ctx, double *out) {
 int lee_state_bytes(lee_ctx *ctx, long long *bytes) {
     if (!ctx || !bytes) return LEE_ERR_ARG;
     if (!ctx->bound) return fail(ctx, LEE_ERR_ARG, "not bound");
-    *bytes = 16 + 3 * ctx->hd.plane * (long long)ctx->elem() + 16LL * ctx->hd.ng + 8LL * ctx->hd.np * ctx->hd.pcap;
+    *bytes = 16 + 3 * ctx->hd.plane * (long long)ctx->elem() + 8LL * ctx->hd.ns * ctx->hd.ng +
+             8LL * ctx->hd.np * ctx->hd.pcap;
     return LEE_OK;
 }
 
@@ -701,8 +735,9 @@ int lee_read_state(lee_ctx *ctx, void *blob) {
     const size_t qb = 3 * (size_t)ctx->hd.plane * ctx->elem();
     CK(cudaMemcpyAsync(b, ctx->hd.clock, 16, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(b + 16, ctx->hd.q[0], qb, cudaMemcpyDeviceToHost, ctx->stream));
-    if (ctx->hd.ng) CK(cudaMemcpyAsync(b + 16 + qb, ctx->hd.Xn, 16 * (size_t)ctx->hd.ng, cudaMemcpyDeviceToHost, ctx->stream));
-    if (ctx->hd.np) CK(cudaMemcpyAsync(b + 16 + qb + 16 * (size_t)ctx->hd.ng, ctx->hd.p_hist,
+    const size_t xb = 8 * (size_t)ctx->hd.ns * ctx->hd.ng;
+    if (ctx->hd.ng) CK(cudaMemcpyAsync(b + 16 + qb, ctx->hd.Xn, xb, cudaMemcpyDeviceToHost, ctx->stream));
+    if (ctx->hd.np) CK(cudaMemcpyAsync(b + 16 + qb + xb, ctx->hd.p_hist,
                                        8 * (size_t)ctx->hd.np * ctx->hd.pcap, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return LEE_OK;
@@ -717,11 +752,12 @@ int lee_write_state(lee_ctx *ctx, const void *blob) {
     CK(cudaMemcpyAsync(ctx->hd.clock, b, 16, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemsetAsync(ctx->hd.clock + 2, 0, sizeof(long long), ctx->stream));   // status: healthy
     CK(cudaMemcpyAsync(ctx->hd.q[0], b + 16, qb, cudaMemcpyHostToDevice, ctx->stream));
+    const size_t xb = 8 * (size_t)ctx->hd.ns * ctx->hd.ng;
     if (ctx->hd.ng) {
-        CK(cudaMemcpyAsync(ctx->hd.Xn, b + 16 + qb, 16 * (size_t)ctx->hd.ng, cudaMemcpyHostToDevice, ctx->stream));
-        CK(cudaMemcpyAsync(ctx->hd.Xs, b + 16 + qb, 16 * (size_t)ctx->hd.ng, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->hd.Xn, b + 16 + qb, xb, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->hd.Xs, b + 16 + qb, xb, cudaMemcpyHostToDevice, ctx->stream));
     }
-    if (ctx->hd.np) CK(cudaMemcpyAsync(ctx->hd.p_hist, b + 16 + qb + 16 * (size_t)ctx->hd.ng,
+    if (ctx->hd.np) CK(cudaMemcpyAsync(ctx->hd.p_hist, b + 16 + qb + xb,
                                        8 * (size_t)ctx->hd.np * ctx->hd.pcap, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return LEE_OK;
@@ -736,9 +772,10 @@ int lee_upload_state_async(lee_ctx *ctx, const void *blob) {
     CK(cudaMemcpyAsync(ctx->hd.clock, b, 16, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemsetAsync(ctx->hd.clock + 2, 0, sizeof(long long), ctx->stream));   // status: healthy
     CK(cudaMemcpyAsync(ctx->hd.q[0], b + 16, qb, cudaMemcpyHostToDevice, ctx->stream));
+    const size_t xb = 8 * (size_t)ctx->hd.ns * ctx->hd.ng;
     if (ctx->hd.ng) {
-        CK(cudaMemcpyAsync(ctx->hd.Xn, b + 16 + qb, 16 * (size_t)ctx->hd.ng, cudaMemcpyHostToDevice, ctx->stream));
-        CK(cudaMemcpyAsync(ctx->hd.Xs, b + 16 + qb, 16 * (size_t)ctx->hd.ng, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->hd.Xn, b + 16 + qb, xb, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->hd.Xs, b + 16 + qb, xb, cudaMemcpyHostToDevice, ctx->stream));
     }
     return LEE_OK;
 }
@@ -925,6 +962,8 @@ static int batch_refresh(lee_batch *b) {
     bv.total_tiles = tp[n];
     bv.total_ghosts = total_ghosts;
     bv.precision = b->precision;
+    bv.ade_general = 0;
+    for (size_t i = 0; i < n; ++i) bv.ade_general |= descs[i].ns != 2;
     drop_graphs(b->graph);
     b->dirty = false;
     return LEE_OK;

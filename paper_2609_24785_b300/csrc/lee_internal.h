@@ -26,6 +26,7 @@ constexpr int HALO = 4;                 // smem halo on each side (the 7-pt DRP 
                                         // the TMA box origin 16-byte aligned); band nodes read
                                         // their one-sided windows from global memory
 constexpr int MAX_PROBES = 1024;
+constexpr int MAX_ADE_STATES = 8;       // ADE states per ghost of a rational admittance (N + 2M)
 
 // status word of an instance (InstDesc::clock[2]), set on the device
 constexpr unsigned long long STATUS_TIMEOUT = 1ull;    // a bounded wait for a tile copy gave up
@@ -101,6 +102,8 @@ struct alignas(16) InstDesc {
     double *scratch;            // reductions
     double *staging;            // nx * ny doubles for host transfers
     const double *bc;           // ng x 2 boundary data (u.n, dp/dn) of the ghost-fill test hook
+    const double *ade;          // ns > 2: A (ns x ns, row-major), b (ns), c (ns) of X' = A X + b p_BP, u_n = c.X
+    int ns;                     // ADE states per ghost (2: MSD wall or rigid; N + 2M: rational admittance)
     int precision;
     int sponge_w;               // absorbing ramp width in cells (0: no ramp)
 };
@@ -125,6 +128,8 @@ struct Plan {
     // ADE
     int regime = 0;
     double A[4] = {0, 0, 0, 0}, b[2] = {0, 0}, c[2] = {0, 0};
+    int ns = 2;                         // states per ghost
+    std::vector<double> ade_coef;       // ns > 2: A (ns x ns), b (ns), c (ns)
     double ade_amp = 0;
     // probes
     std::vector<int> p_idx;             // np x 16 host order
@@ -139,6 +144,12 @@ struct Geometry {
 struct Impedance {
     bool rigid = true;
     double R = 0, M = 0, K = 0;
+    // rational admittance (Sec. 2.3, Eq. Yrational with Y_inf = 0): nreal real
+    // poles lam with residues A, npair pairs al +- i be with residues B +- i C
+    int nreal = 0, npair = 0;
+    double lam[MAX_ADE_STATES] = {}, A[MAX_ADE_STATES] = {};
+    double al[MAX_ADE_STATES] = {}, be[MAX_ADE_STATES] = {}, B[MAX_ADE_STATES] = {}, C[MAX_ADE_STATES] = {};
+    bool rational() const { return !rigid && nreal + npair > 0; }
 };
 
 // host set-up (lee_setup.cpp); returns LEE_* status, message in err
@@ -166,6 +177,7 @@ struct BatchView {
     int total_tiles;
     int total_ghosts;
     int precision;
+    int ade_general;            // some instance has ns > 2: the ghost kernel's general ADE variant
 };
 cudaError_t prepare_kernels(int precision);   // one-time function attributes (outside capture)
 int num_sms();

@@ -140,7 +140,11 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // for that stage.  stage 0 (test hook lee_fill_ghosts_with_bc): the ghosts of
 // Q^n are filled from the boundary data d.bc (u.n and dp/dn at each boundary
 // point) instead of the ADE's, and no ADE state or clock changes.
-template <typename T, int GA>
+// GEN: the general ADE of a rational admittance (Sec. 2.3, Eq. ADEgeneral as
+// X' = A X + b p_BP, u_n = c . X with d.ns states per ghost and the dense
+// coefficients d.ade); GEN = false is the two-state form of the MSD wall
+// (Sec. 2.5) and of the rigid wall, with its coefficients in the descriptor.
+template <typename T, int GA, bool GEN = false>
 __global__ void __launch_bounds__(GHOST_THREADS, GA == GA_FF ? 5 : 0)   // float-float: 5 CTAs per SM; others unconstrained
 ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int4 *__restrict__ chunks, int nchunks,
              int stage) {
@@ -164,14 +168,18 @@ ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int4 *__restric
     int t = 0;
     if (lane == 0) {
         if constexpr (GA == GA_FF) {
-            cp_async16(&s_x[sub], d.Xs + 2 * g);            // 16-byte aligned: 2 doubles per ghost
-            cp_async16(&s_xn[sub], d.Xn + 2 * g);
+            if constexpr (!GEN) {
+                cp_async16(&s_x[sub], d.Xs + 2 * g);        // 16-byte aligned: 2 doubles per ghost
+                cp_async16(&s_xn[sub], d.Xn + 2 * g);
+            }
             cp_async16(&s_n[sub], d.g_n + g);
             cp_async16(&s_k[sub], d.g_kappa + g);
             cp_async4(&s_t[sub], d.g_target + g);
         } else {
-            x0 = d.Xs[2 * g]; x1 = d.Xs[2 * g + 1];
-            xn0 = d.Xn[2 * g]; xn1 = d.Xn[2 * g + 1];
+            if constexpr (!GEN) {
+                x0 = d.Xs[2 * g]; x1 = d.Xs[2 * g + 1];
+                xn0 = d.Xn[2 * g]; xn1 = d.Xn[2 * g + 1];
+            }
             n = __ldg(d.g_n + g);
             kap = __ldg(d.g_kappa + g);
             t = __ldg(d.g_target + g);
@@ -267,8 +275,10 @@ ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int4 *__restric
     if (lane != 0) return;
     if constexpr (GA == GA_FF) {
         cp_async_wait_all();                           // this thread's own copies
-        x0 = s_x[sub].x; x1 = s_x[sub].y;
-        xn0 = s_xn[sub].x; xn1 = s_xn[sub].y;
+        if constexpr (!GEN) {
+            x0 = s_x[sub].x; x1 = s_x[sub].y;
+            xn0 = s_xn[sub].x; xn1 = s_xn[sub].y;
+        }
         n = s_n[sub];
         kap = s_k[sub];
         t = s_t[sub];
@@ -284,6 +294,50 @@ ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int4 *__restric
         return;
     }
     const double pbp = s0;
+    if constexpr (GEN) {
+        // steps 2-3 for ns states: X' = A X + b p_BP, u_n = c . X, du_n = c . X'
+        const int ns = d.ns;
+        const double *Am = d.ade, *bv = Am + ns * ns, *cv = bv + ns;
+        double xv[MAX_ADE_STATES], xd[MAX_ADE_STATES];
+#pragma unroll
+        for (int i = 0; i < MAX_ADE_STATES; ++i) xv[i] = i < ns ? d.Xs[(long long)ns * g + i] : 0.0;
+        double un = 0.0, dun = 0.0;
+#pragma unroll
+        for (int i = 0; i < MAX_ADE_STATES; ++i) {
+            if (i < ns) {
+                double a = bv[i] * pbp;
+#pragma unroll
+                for (int j = 0; j < MAX_ADE_STATES; ++j)
+                    if (j < ns) a = fma(Am[i * ns + j], xv[j], a);
+                xd[i] = a;
+                un = fma(cv[i], xv[i], un);
+                dun = fma(cv[i], a, dun);
+            } else {
+                xd[i] = 0.0;
+            }
+        }
+        // steps 4-5 as below
+        const double pg = s1 + kap.x * dun;
+        const double wg = n.x * s2 + n.y * s3 - kap.y * un;
+        const double tg = -n.y * s4 + n.x * s5;
+        P[t] = (T)pg;
+        U[t] = (T)(wg * n.x - tg * n.y);
+        V[t] = (T)(wg * n.y + tg * n.x);
+        const double ad = d.kd[stage - 1][K_AD];
+        bool fin = isfinite(pbp);
+#pragma unroll
+        for (int i = 0; i < MAX_ADE_STATES; ++i) {
+            if (i < ns) {
+                const long long o = (long long)ns * g + i;
+                const double y = d.Xn[o] + ad * xd[i];
+                d.Xs[o] = y;
+                if (stage == 4) d.Xn[o] = y;
+                fin = fin && isfinite(y);
+            }
+        }
+        if (!fin) atomicOr((unsigned long long *)&d.clock[2], STATUS_DIVERGED);
+        return;
+    }
     // step 2: ADE derivative with p_BP as forcing
     const double xd0 = d.A[0] * x0 + d.A[1] * x1 + d.b[0] * pbp;
     const double xd1 = d.A[2] * x0 + d.A[3] * x1 + d.b[1] * pbp;
@@ -360,9 +414,18 @@ __device__ __forceinline__ int band_window(int x, int n, int per, int &t) {
 // sum_j C[t][j] (w_j - w_t) / h: the node's own value is taken out of every
 // term, which keeps the derivative of a constant exactly zero with rounded
 // coefficients
+// w[t] by selects (a dynamic index would put the window in local memory)
+template <typename T>
+__device__ __forceinline__ T pick7(const T (&w)[7], int t) {
+    T r = w[0];
+#pragma unroll
+    for (int j = 1; j < 7; ++j) r = t == j ? w[j] : r;
+    return r;
+}
+
 template <typename T>
 __device__ __forceinline__ T band_deriv(const T (&w)[7], int t, T inv_h) {
-    const T wt = w[t];
+    const T wt = pick7(w, t);
     T s = T(0);
 #pragma unroll
     for (int j = 0; j < 7; ++j) s += band_coef<T>(t, j) * (w[j] - wt);
@@ -455,7 +518,7 @@ __device__ __forceinline__ void band_point(const T *__restrict__ gin, const QnSr
         ct = rx / rho; st = ryy / rho; q2 = half_inv_h / rho;
     }
     const T sg = sk_h * ramp2<T>(d, gx, gy);
-    const T p0 = wx[0][tx], u0 = wx[1][tx], v0 = wx[2][tx];
+    const T p0 = pick7(wx[0], tx), u0 = pick7(wx[1], tx), v0 = pick7(wx[2], tx);
     const T rp = -(ct * dpdx + st * dpdy + p0 * q2) - sg * p0;
     const T ru = -(ct * dudx + st * dudy + u0 * q2) - sg * u0;
     const T rv = -(ct * dvdx + st * dvdy + v0 * q2) - sg * v0;
@@ -1443,14 +1506,23 @@ cudaError_t launch_ghost(const BatchView &bv, int stage, cudaStream_t s) {
         const char *e = getenv("LEE_GHOST_WIDEN");
         return !(e && std::string(e) == "hw");
     }();
-    if (ghost_float_float(bv.precision))
-        ghost_kernel<float, GA_FF><<<blocks, GHOST_THREADS, 0, s>>>(bv.inst, bv.ninst, bv.ghost_chunks, bv.nchunks, stage);
+    const InstDesc *in = bv.inst;
+    const int4 *ch = bv.ghost_chunks;
+    if (bv.ade_general) {               // some instance has a rational admittance (ns != 2)
+        if (ghost_float_float(bv.precision))
+            ghost_kernel<float, GA_FF, true><<<blocks, GHOST_THREADS, 0, s>>>(in, bv.ninst, ch, bv.nchunks, stage);
+        else if (bv.precision == 1)
+            ghost_kernel<float, GA_F64_INT, true><<<blocks, GHOST_THREADS, 0, s>>>(in, bv.ninst, ch, bv.nchunks, stage);
+        else
+            ghost_kernel<double, GA_F64_HW, true><<<blocks, GHOST_THREADS, 0, s>>>(in, bv.ninst, ch, bv.nchunks, stage);
+    } else if (ghost_float_float(bv.precision))
+        ghost_kernel<float, GA_FF><<<blocks, GHOST_THREADS, 0, s>>>(in, bv.ninst, ch, bv.nchunks, stage);
     else if (bv.precision == 1 && intw)
-        ghost_kernel<float, GA_F64_INT><<<blocks, GHOST_THREADS, 0, s>>>(bv.inst, bv.ninst, bv.ghost_chunks, bv.nchunks, stage);
+        ghost_kernel<float, GA_F64_INT><<<blocks, GHOST_THREADS, 0, s>>>(in, bv.ninst, ch, bv.nchunks, stage);
     else if (bv.precision == 1)
-        ghost_kernel<float, GA_F64_HW><<<blocks, GHOST_THREADS, 0, s>>>(bv.inst, bv.ninst, bv.ghost_chunks, bv.nchunks, stage);
+        ghost_kernel<float, GA_F64_HW><<<blocks, GHOST_THREADS, 0, s>>>(in, bv.ninst, ch, bv.nchunks, stage);
     else
-        ghost_kernel<double, GA_F64_HW><<<blocks, GHOST_THREADS, 0, s>>>(bv.inst, bv.ninst, bv.ghost_chunks, bv.nchunks, stage);
+        ghost_kernel<double, GA_F64_HW><<<blocks, GHOST_THREADS, 0, s>>>(in, bv.ninst, ch, bv.nchunks, stage);
     count_launch();
     return cudaGetLastError();
 }

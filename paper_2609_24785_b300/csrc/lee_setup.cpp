@@ -358,8 +358,45 @@ int build_plan(int nx, int ny, double h, double x0, double y0, int per_x, int pe
         P.e_w.insert(P.e_w.end(), out[g].w.begin(), out[g].w.end());
     }
 
-    // ---- ADE of the MSD wall (Sec. 2.5)
-    if (imp.rigid) {
+    // ---- ADE of the MSD wall (Sec. 2.5), or of a rational admittance (Sec. 2.3)
+    if (imp.rational()) {
+        // Eq. ADEgeneral as X' = A X + b p_BP, u_n = c . X (Eq. unGeneral),
+        // A block diagonal: one 1 x 1 block per real pole, one rotation block
+        // [[al, -be], [be, al]] per pair
+        const int ns = imp.nreal + 2 * imp.npair;
+        P.regime = 4;
+        P.ns = ns;
+        P.ade_coef.assign((size_t)ns * ns + 2 * ns, 0.0);
+        double *A = P.ade_coef.data(), *b = A + (size_t)ns * ns, *c = b + ns;
+        double amp = 0.0;
+        for (int k = 0; k < imp.nreal; ++k) {
+            if (!(imp.lam[k] < 0)) { err = "rational admittance: real poles must be negative"; return LEE_ERR_ARG; }
+            A[(size_t)k * ns + k] = imp.lam[k];
+            b[k] = 1.0;
+            c[k] = imp.A[k];
+            amp = std::max(amp, std::abs(rk4_poly(std::complex<double>(imp.lam[k] * dt, 0.0))));
+        }
+        for (int k = 0; k < imp.npair; ++k) {
+            if (!(imp.al[k] < 0 && imp.be[k] > 0)) {
+                err = "rational admittance: pairs need alpha < 0 < beta";
+                return LEE_ERR_ARG;
+            }
+            const int i = imp.nreal + 2 * k;
+            A[(size_t)i * ns + i] = imp.al[k];
+            A[(size_t)i * ns + i + 1] = -imp.be[k];
+            A[(size_t)(i + 1) * ns + i] = imp.be[k];
+            A[(size_t)(i + 1) * ns + i + 1] = imp.al[k];
+            b[i] = 1.0;
+            c[i] = 2.0 * imp.B[k];
+            c[i + 1] = -2.0 * imp.C[k];
+            amp = std::max(amp, std::abs(rk4_poly(std::complex<double>(imp.al[k], imp.be[k]) * dt)));
+        }
+        P.ade_amp = amp;
+        if (ns == 2) {          // the two-state kernel path takes it like an MSD wall
+            for (int q = 0; q < 4; ++q) P.A[q] = A[q];
+            P.b[0] = b[0]; P.b[1] = b[1]; P.c[0] = c[0]; P.c[1] = c[1];
+        }
+    } else if (imp.rigid) {
         P.regime = 0;
         P.ade_amp = 0.0;
     } else {
@@ -399,6 +436,11 @@ int build_plan(int nx, int ny, double h, double x0, double y0, int per_x, int pe
         }
         P.ade_amp = std::max(std::abs(rk4_poly(p1 * dt)), std::abs(rk4_poly(p2 * dt)));
     }
+
+    // the two-state forms in the dense layout as well, so that a batch whose
+    // ghost kernel runs the general ADE (some member has ns != 2) takes them too
+    if (P.ade_coef.empty())
+        P.ade_coef = {P.A[0], P.A[1], P.A[2], P.A[3], P.b[0], P.b[1], P.c[0], P.c[1]};
 
     // ---- probes: 4 x 4 Lagrange (degree 3), else nearest fluid node
     const int np = (int)probe_xy.size() / 2;

@@ -40,7 +40,8 @@ class lee_grid(C.Structure):
 class lee_sizes(C.Structure):
     _fields_ = [("device_bytes", C.c_longlong), ("n_ghost", C.c_int), ("n_fluid", C.c_int),
                 ("n_entries", C.c_longlong), ("n_reduced", C.c_int), ("regime", C.c_int),
-                ("dt", C.c_double), ("ade_amplification", C.c_double), ("n_tiles", C.c_int)]
+                ("dt", C.c_double), ("ade_amplification", C.c_double), ("n_tiles", C.c_int),
+                ("n_states", C.c_int)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -61,6 +62,8 @@ SIGNATURES = {
     "lee_set_tile": (C.c_int, [_vp, C.c_int, C.c_int]),
     "lee_set_sponge": (C.c_int, [_vp, C.c_int, C.c_double]),
     "lee_fill_ghosts_with_bc": (C.c_int, [_vp, _dp]),
+    "lee_set_impedance_rational": (C.c_int, [_vp, C.c_int, _dp, C.c_int, _dp]),
+    "lee_fp64_fma_probe": (C.c_int, [C.c_int, C.c_longlong, _vp, _vp]),
     "lee_plan": (C.c_int, [_vp, C.POINTER(lee_sizes)]),
     "lee_bind": (C.c_int, [_vp, _vp, C.c_longlong, _vp]),
     "lee_init_pulse": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double, C.c_double]),
@@ -179,6 +182,16 @@ class Solver:
     def set_impedance(self, R, M, K):
         self._c(self.L.lee_set_impedance(self.ctx, R, M, K)); return self
 
+    def set_impedance_rational(self, real=(), pairs=()):
+        """Rational admittance of Sec. 2.3 (Y_inf = 0): real = [(lam, A)],
+        pairs = [(alpha, beta, B, C)]."""
+        r = np.ascontiguousarray(np.asarray(real, dtype=np.float64).reshape(-1, 2))
+        q = np.ascontiguousarray(np.asarray(pairs, dtype=np.float64).reshape(-1, 4))
+        rb = r if r.size else np.zeros(2)
+        qb = q if q.size else np.zeros(4)
+        self._c(self.L.lee_set_impedance_rational(self.ctx, len(r), _d(rb), len(q), _d(qb)))
+        return self
+
     def set_rigid(self):
         self._c(self.L.lee_set_rigid(self.ctx)); return self
 
@@ -248,10 +261,10 @@ class Solver:
         return out.reshape(self.ny, self.nx)
 
     def ade(self):
-        ng = self.sizes.n_ghost
-        out = np.zeros(2 * max(ng, 1))
+        ng, ns = self.sizes.n_ghost, self.sizes.n_states
+        out = np.zeros(ns * max(ng, 1))
         self._c(self.L.lee_read_ade(self.ctx, _d(out)))
-        return out[:2 * ng].reshape(-1, 2)
+        return out[:ns * ng].reshape(-1, ns)
 
     def steps_done(self):
         v = C.c_longlong()

@@ -17,12 +17,14 @@ import numpy as np
 
 H = 0.01
 CFL = 0.5
-# Opt-in absorbing ramp (width in cells, kappa) of the FP32 workloads that run
-# thousands of steps (sweep, serving, monopole): the outer one-sided/radiation
-# closure amplifies FP32 rounding (its grid-scale modes grow slowly), and this
-# ramp damps them.  The paper adds no damping; the FP64 parity cases run
+# Opt-in absorbing ramp (width in cells, kappa) of the workloads that run
+# thousands of steps (cylinder pulse, sweep, serving, monopole): the outer
+# one-sided/radiation closure has slowly growing grid-scale modes that amplify
+# rounding (a 1e-16 difference reaches 3e-11 in 3000 steps on the 1024^2
+# cylinder, FP32 rounding 5e-3), and this ramp damps them.  The paper adds no
+# damping; the flat-wall workload (400 steps) and the short parity cases run
 # without it.
-FP32_SPONGE = (12, 0.04)
+LONG_RUN_SPONGE = (12, 0.04)
 
 
 @dataclass
@@ -33,7 +35,7 @@ class Case:
     h: float = H
     cfl: float = CFL
     wall: Tuple = ("none",)            # ("line", xw, yw, angle) | ("cyl", xc, yc, r) | ("none",)
-    imp: Tuple = ("rigid",)            # ("rigid",) | ("msd", R, M, K)
+    imp: Tuple = ("rigid",)            # ("rigid",) | ("msd", R, M, K) | ("rational", [(lam, A)], [(al, be, B, C)])
     init: Tuple = ("zero",)            # ("pulse", xs, ys, amp, w) | ("packet", xs, ys, ang, amp, k, alpha)
     source: Optional[Tuple] = None     # ("monopole", xs, ys, amp, w, omega)
     probes: np.ndarray = field(default_factory=lambda: np.zeros((0, 2)))
@@ -64,11 +66,13 @@ def flat_wall(n=128, angle_deg=30.0, steps=400, R=1.0, M=0.05, K=5.0, rigid=Fals
                 init=("pulse", src[0], src[1], 1e-3, 3 * H), probes=probes, steps=steps)
 
 
-def cylinder_pulse(n=1024, steps=3000, R=2.0, M=0.02, K=1.0, rigid=False, nx=None, ny=None) -> Case:
+def cylinder_pulse(n=1024, steps=3000, R=2.0, M=0.02, K=1.0, rigid=False, nx=None, ny=None,
+                   sponge=LONG_RUN_SPONGE) -> Case:
     """Cylinder of radius n/20.48 cells (50 at n = 1024) at the centre, Gaussian
     pulse of half-width 4n/1024 cells and amplitude 1 at n/10.24 cells on +x;
-    8 probes on a ring of 1.5 radii.  The physical problem is the same for every
-    n when h = 0.01 * 1024 / n (refinement sweeps pass h explicitly)."""
+    8 probes on a ring of 1.5 radii; the long-run absorbing ramp by default.
+    The physical problem is the same for every n when h = 0.01 * 1024 / n
+    (refinement sweeps pass h explicitly)."""
     nx = nx or n
     ny = ny or n
     c = ((nx - 1) / 2 * H, (ny - 1) / 2 * H)
@@ -79,14 +83,14 @@ def cylinder_pulse(n=1024, steps=3000, R=2.0, M=0.02, K=1.0, rigid=False, nx=Non
     probes = np.stack([c[0] + 1.5 * r * np.cos(ang), c[1] + 1.5 * r * np.sin(ang)], 1)
     return Case("cylinder_pulse_%dx%d" % (nx, ny), nx, ny, wall=("cyl", c[0], c[1], r),
                 imp=("rigid",) if rigid else ("msd", R, M, K),
-                init=("pulse", xs, c[1], 1.0, w), probes=probes, steps=steps)
+                init=("pulse", xs, c[1], 1.0, w), probes=probes, steps=steps, sponge=sponge)
 
 
 def monopole(n=2048, steps=20000, R=1.0, M=0.1, K=10.0, radius_cells=None, src_cells=None,
-             nring=256, sponge=FP32_SPONGE) -> Case:
+             nring=256, sponge=LONG_RUN_SPONGE) -> Case:
     """Cylinder of radius n/20.48 cells scattering a harmonic monopole at
     3 radii on +x (half-width 3 cells, amplitude 1, 20 points per wavelength);
-    probe ring of nring points at 1.1 radii; the FP32 absorbing ramp by
+    probe ring of nring points at 1.1 radii; the long-run absorbing ramp by
     default (20000 steps)."""
     c = ((n - 1) / 2 * H, (n - 1) / 2 * H)
     rc = (radius_cells if radius_cells is not None else n / 20.48) * H
@@ -103,10 +107,10 @@ SWEEP_SIZES = (256, 384, 512, 768, 1024)
 
 
 def sweep(count=512, seed=24785, steps=2000, accept: Optional[Callable[[Case], bool]] = None,
-          sizes=SWEEP_SIZES, sponge=FP32_SPONGE) -> Tuple[List[Case], int]:
+          sizes=SWEEP_SIZES, sponge=LONG_RUN_SPONGE) -> Tuple[List[Case], int]:
     """Batched parametric sweep: grid n uniform in `sizes`, cylinder radius 0.1 n
     cells at the centre, pulse (half-width 4 cells) at 0.25 n cells on +x, R, M,
-    K log-uniform in [0.2, 5], [0.005, 0.2], [0.5, 20], the FP32 absorbing
+    K log-uniform in [0.2, 5], [0.005, 0.2], [0.5, 20], the long-run absorbing
     ramp.  Draws rejected by `accept` (e.g. an unstable wall ODE) are redrawn
     from the same stream; returns (cases, rejected)."""
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -131,12 +135,12 @@ SERVE_SIZES = (256, 384, 512, 768, 1024, 1536, 2048)
 
 
 def serving_trace(rate=200.0, duration=1.0, seed=24786, accept=None, sizes=SERVE_SIZES,
-                  steps_range=(1000, 10000), sponge=FP32_SPONGE) -> List[Tuple[float, Case]]:
+                  steps_range=(1000, 10000), sponge=LONG_RUN_SPONGE) -> List[Tuple[float, Case]]:
     """Poisson arrivals (mean `rate` per second over `duration` seconds) of mixed
     solves: half flat walls through the centre at an angle U[0, 60] deg, half
     cylinders of radius U[0.05, 0.15] n; pulse of half-width 4 cells at a
     uniform position at least 20 cells from the wall and the edges; R, M, K as
-    in the sweep; steps uniform in steps_range; the FP32 absorbing ramp
+    in the sweep; steps uniform in steps_range; the long-run absorbing ramp
     (flat walls meet the radiation band, and runs last up to 10000 steps)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     t, out = 0.0, []
@@ -185,6 +189,8 @@ def apply_to(case: Case, target):
         (target.set_wall_none if hasattr(target, "set_wall_none") else target.set_none)()
     if case.imp[0] == "msd":
         target.set_impedance(*case.imp[1:])
+    elif case.imp[0] == "rational":
+        target.set_impedance_rational(*case.imp[1:])
     else:
         target.set_rigid()
     if case.sponge[0] > 0:
@@ -201,3 +207,23 @@ def apply_state(case: Case, target):
     elif case.init[0] == "packet":
         target.init_packet(*case.init[1:])
     return target
+
+
+def flat_wall_paper(h=0.005, rigid=False, t_end=2.0) -> Case:
+    """The flat immersed wall of Sec. 4.1: domain [-1, 0.8] x [-0.2, 0.2]
+    (shifted here by (+1, +0.2) so that node (0, 0) sits at the origin),
+    periodic in y, radiation condition at x = -1; wall normal to x at
+    x = 0.6 + h/2 (fluid on the left); wave packet p0 = (a/2) exp(-alpha^2 x^2)
+    cos(2 pi k x), u0 = p0, v0 = 0, a = 1, k = 7, alpha = k / sqrt(0.8), at
+    x = 0; MSD wall M = 0.025, K = 40, R = 0.2 (or rigid); CFL 0.5; probe at
+    the microphone (0.5, 0); t_end = 2."""
+    nx = int(round(1.8 / h)) + 1
+    ny = int(round(0.4 / h))
+    k = 7.0
+    xw = 1.6 + h / 2
+    steps = int(round(t_end / (CFL * h)))
+    return Case("flat_wall_paper_h%g%s" % (h, "_rigid" if rigid else ""), nx, ny, h=h,
+                wall=("line", xw, 0.2, math.pi / 2),
+                imp=("rigid",) if rigid else ("msd", 0.2, 0.025, 40.0),
+                init=("packet", 1.0, 0.2, 0.0, 1.0, k, k / math.sqrt(0.8)),
+                probes=np.array([[1.5, 0.2]]), steps=steps, periodic=(False, True))

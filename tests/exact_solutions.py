@@ -28,3 +28,78 @@ def free_pulse(r, t, a, b, nk=4000):
     p = (np.cos(k * t) * wk) @ j0(kr)
     ur = (np.sin(k * t) * wk) @ j1(kr)
     return p.reshape(r.shape), ur.reshape(r.shape)
+
+
+def flat_wall_signal(F, t, x_mic, x_wall, Z=None):
+    """App. A: pressure at x_mic (fluid at x < x_wall) of the incident simple
+    wave F(x - t) and its reflection from a locally reacting wall,
+        p(x_m, t) = F(x_m - t) + r(t - (x_wall - x_m)),
+    r = R_c * F(x_wall - tau) with R_c(w) = (Z - 1)/(Z + 1) applied by FFT
+    (Z(s) with s = i w; Z = None is the rigid wall, R_c = 1).  t must be a
+    uniform grid t_n = (n + 1) dt on which the travel time x_wall - x_mic is a
+    whole number of steps; the filtered signal is sampled on the same step
+    over a window long enough for it to decay."""
+    t = np.asarray(t, dtype=np.float64)
+    dt = t[1] - t[0]
+    delay = (x_wall - x_mic) / dt
+    nd = int(round(delay))
+    assert abs(delay - nd) < 1e-6, "travel time must be a whole number of steps"
+    T = 1 << int(np.ceil(np.log2(4 * (len(t) + nd) + 1024)))
+    tau = np.arange(T) * dt
+    sig = F(x_wall - tau)
+    w = 2 * np.pi * np.fft.fftfreq(T, dt)
+    if Z is None:
+        Rc = np.ones(T, dtype=complex)
+    else:
+        s = 1j * w
+        s[0] = 1e-300j
+        z = Z(s)
+        Rc = (z - 1) / (z + 1)
+        Rc[0] = 1.0                      # a spring: Z -> infinity as s -> 0, R_c -> 1
+    refl = np.real(np.fft.ifft(Rc * np.fft.fft(sig)))
+    # r at times t - (x_wall - x_mic): index n + 1 - nd on the tau grid
+    idx = np.round(t / dt).astype(int) - nd
+    r = np.where(idx >= 0, refl[np.clip(idx, 0, T - 1)], 0.0)
+    return F(x_mic - t) + r
+
+
+def monopole_cylinder(x, y, xs, ys, xc, yc, a_cyl, omega, amp, w, Z=None, nextra=40):
+    """App. C: complex pressure amplitude P (p = Im(P e^{i w t})) of the
+    harmonic Gaussian monopole s = amp exp(-b |x - xs|^2) sin(w t),
+    b = ln 2 / w^2, scattered by a cylinder of radius a_cyl at (xc, yc) with
+    impedance Z(w) = R + i (M w - K / w) (None: rigid), c = rho = 1, k = w:
+        P = C H0(k |x - xs|) + C sum_n eps_n H_n(k r_s) S_n H_n(k r) cos(n (th - th_s)),
+        C = (w / 4) amp (pi / b) exp(-k^2 / 4b),
+        S_n = -(J_n(ka) + i Z J_n'(ka)) / (H_n(ka) + i Z H_n'(ka))   (H = H^(2)),
+    the Graf re-expansion of the incident field about the cylinder axis
+    (valid for r < r_s), truncated at N = ceil(ka) + nextra modes."""
+    from scipy.special import hankel2, h2vp, jv, jvp
+    k = float(omega)
+    b = np.log(2.0) / w ** 2
+    C = (omega / 4.0) * amp * (np.pi / b) * np.exp(-k * k / (4.0 * b))
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    r = np.hypot(x - xc, y - yc)
+    th = np.arctan2(y - yc, x - xc)
+    rs = np.hypot(xs - xc, ys - yc)
+    ths = np.arctan2(ys - yc, xs - xc)
+    assert np.all(r < rs), "the Graf expansion holds inside the source radius"
+    ka = k * a_cyl
+    N = int(np.ceil(ka)) + nextra
+    P = C * hankel2(0, k * np.hypot(x - xs, y - ys))
+    for n in range(N + 1):
+        eps = 1.0 if n == 0 else 2.0
+        if Z is None:
+            S = -jvp(n, ka) / h2vp(n, ka)
+        else:
+            S = -(jv(n, ka) + 1j * Z * jvp(n, ka)) / (hankel2(n, ka) + 1j * Z * h2vp(n, ka))
+        P = P + C * eps * hankel2(n, k * rs) * S * hankel2(n, k * r) * np.cos(n * (th - ths))
+    return P
+
+
+def harmonic_amplitude(p, t, omega):
+    """Least-squares fit p(t) = Re(P) sin(w t) + Im(P) cos(w t) (i.e.
+    p = Im(P e^{i w t})) over the samples; returns P per column of p."""
+    A = np.stack([np.sin(omega * t), np.cos(omega * t)], 1)
+    coef, *_ = np.linalg.lstsq(A, np.asarray(p, dtype=np.float64), rcond=None)
+    return coef[0] + 1j * coef[1]

@@ -58,3 +58,32 @@ def test_cylinder_pulse_converges(rigid, cuda_device):
         "rigid" if rigid else "impedance", ["%.2e" % e for e in errs], ["%.2f" % o for o in orders], mean))
     assert errs[0] > errs[1] > errs[2]
     assert mean >= 3.0, (errs, orders)
+
+
+@pytest.mark.parametrize("rigid", [False, True], ids=["impedance", "rigid"])
+def test_paper_flat_wall_converges_on_gpu(rigid, cuda_device):
+    """The flat immersed wall of Sec. 4.1 at the paper's grids h = 0.01, 0.005,
+    0.0025 and one finer, 0.00125 (FP64 bulk, periodic in y, radiation
+    condition at x = -1), against the App. A exact microphone signal: every
+    successive order is at least 3.8 (the paper: 4 in Sec. 4.1, about 4.5 in
+    its conclusion), and the h = 0.005 run equals the oracle's to 1e-12."""
+    import sys, os
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from test_oracle_pins import _paper_flat_wall_error
+    from _helpers import make_oracle, log_result, rel_l2
+
+    def run(case):
+        s = make_solver(case, "fp64")
+        s.step(case.steps)
+        s.sync()
+        return s.probes()[:, 0]
+    hs = (0.01, 0.005, 0.0025, 0.00125)
+    errs = [_paper_flat_wall_error(h, rigid, run) for h in hs]
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(len(hs) - 1)]
+    log_result("flat wall Sec. 4.1 %s (GPU FP64): errors %s, orders %s" % (
+        "rigid" if rigid else "impedance", ["%.3e" % e for e in errs], ["%.2f" % o for o in orders]))
+    assert min(orders) >= 3.8, (errs, orders)
+    case = workloads.flat_wall_paper(0.005, rigid)
+    o = make_oracle(case)
+    o.run(case.steps)
+    assert rel_l2(run(case), o.probes()[:, 0]) <= 1e-12

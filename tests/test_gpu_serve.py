@@ -27,7 +27,7 @@ def _mixed_cases(k=6):
             pos = (c[0] - 0.25 * n * H * math.sin(th), c[1] + 0.25 * n * H * math.cos(th))
         out.append(workloads.Case("mix%d" % i, n, n, wall=wall, imp=("msd", 0.5 + 0.3 * i, 0.02, 2.0 + i),
                                   init=("pulse", pos[0], pos[1], 1.0, 4 * H), probes=np.array([pos]),
-                                  steps=150 + 97 * i))
+                                  steps=150 + 97 * i, sponge=workloads.LONG_RUN_SPONGE))
     return out
 
 

@@ -160,3 +160,35 @@ def test_autotune_sample_is_size_stratified():
     all_sizes = sorted(c.nx for c in cases)
     assert len(pick) == 10 and sizes[0] == all_sizes[3] and sizes[-1] == all_sizes[57]
     assert autotune.stratified_sample(cases[:5], 10) == cases[:5]
+
+
+def test_rational_admittance_plan():
+    """lee_plan of a rational wall (Sec. 2.3): one state per real pole and two
+    per pair, regime 4, the RK4 amplification max |P(pole dt)| over every pole
+    (computed here from the stability polynomial), and LEE_ERR_ADE_UNSTABLE
+    when a real pole times dt leaves the RK4 interval (about -2.785)."""
+    import math
+    import numpy as np
+    from paper_2609_24785_b300 import lee, workloads
+    case = workloads.flat_wall(64)
+    real = [(-20.0, 5.0), (-200.0, 30.0)]
+    pairs = [(-4.0, 39.8, 20.0, 2.0)]
+    s = lee.Solver(case.nx, case.ny, case.h, case.cfl, precision="fp64")
+    workloads.apply_to(case, s)
+    s.set_impedance_rational(real, pairs)
+    sz = s.plan()
+    assert s.sizes.n_states == 4 and s.sizes.regime == 4
+    dt = case.cfl * case.h
+    P = lambda z: 1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24          # noqa: E731
+    amp = max([abs(P(l * dt)) for l, _ in real] + [abs(P(complex(a, b) * dt)) for a, b, _, _ in pairs])
+    assert abs(s.sizes.ade_amplification - amp) < 1e-12
+    bad = lee.Solver(case.nx, case.ny, case.h, case.cfl, precision="fp64")
+    workloads.apply_to(case, bad)
+    bad.set_impedance_rational([(-3.0 / dt, 1.0)], [])
+    with pytest.raises(lee.LeeError) as e:
+        bad.plan()
+    assert e.value.code == lee.LEE_ERR_ADE_UNSTABLE
+    with pytest.raises(lee.LeeError):
+        lee.Solver(case.nx, case.ny, case.h, case.cfl).set_impedance_rational([(1.0, 1.0)], [])
+    with pytest.raises(lee.LeeError):
+        lee.Solver(case.nx, case.ny, case.h, case.cfl).set_impedance_rational([(-1.0, 1.0)] * 9, [])
