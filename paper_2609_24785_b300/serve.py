@@ -85,6 +85,12 @@ class Report:
             "requests": len(self.requests),
             "completed": len(ok),
             "diverged": sum(r.status == "diverged" for r in self.requests),
+            # which walls diverged: (flat walls, cylinders), and the angles of
+            # the flat walls that did (a straight wall meets the outer band)
+            "diverged_flat_cyl": [sum(r.status == "diverged" and r.case.wall[0] == kind for r in self.requests)
+                                  for kind in ("line", "cyl")],
+            "diverged_flat_angles_deg": sorted(round(math.degrees(r.case.wall[3]), 1) for r in self.requests
+                                               if r.status == "diverged" and r.case.wall[0] == "line"),
             "failed": sum(r.status == "failed" for r in self.requests),
             "p50_s": q(50), "p99_s": q(99), "mean_s": float(lat.mean()) if lat.size else math.nan,
             "mean_wait_s": float(np.mean([r.t_admit - r.arrival for r in ok])) if ok else math.nan,

@@ -227,3 +227,20 @@ def flat_wall_paper(h=0.005, rigid=False, t_end=2.0) -> Case:
                 imp=("rigid",) if rigid else ("msd", 0.2, 0.025, 40.0),
                 init=("packet", 1.0, 0.2, 0.0, 1.0, k, k / math.sqrt(0.8)),
                 probes=np.array([[1.5, 0.2]]), steps=steps, periodic=(False, True))
+
+
+def pulse_cylinder_paper(h=0.04, R=None, M=0.025, K=1.6, t_end=6.0, half=6.0) -> Case:
+    """The pulse-cylinder case of Sec. 4.2: domain [-6, 6]^2 (shifted by +6 so
+    that node (0, 0) sits at the origin), cylinder of radius 0.5 at the
+    centre, Gaussian pulse a = 1, w = 0.2 at (4, 0), radiation condition on
+    all sides, CFL 0.5; MSD wall M = 0.025, K = 1.6 and resistance R (the
+    paper's impedance case R = 0.2; the sweep of Fig. 8b R in {3, 2, 1, 0.5,
+    0.2}), R = None the rigid wall; probe at microphone A (2, 0).  `half` is
+    the half-width of the box (the paper's 6; a wider box moves the outer
+    boundary's reflections out of the recorded window)."""
+    n = int(round(2 * half / h)) + 1
+    c = half
+    return Case("pulse_cylinder_paper_h%g_%s_L%g" % (h, "rigid" if R is None else "R%g" % R, half), n, n, h=h,
+                wall=("cyl", c, c, 0.5), imp=("rigid",) if R is None else ("msd", R, M, K),
+                init=("pulse", c + 4.0, c, 1.0, 0.2), probes=np.array([[c + 2.0, c]]),
+                steps=int(round(t_end / (CFL * h))))

@@ -103,3 +103,58 @@ def harmonic_amplitude(p, t, omega):
     A = np.stack([np.sin(omega * t), np.cos(omega * t)], 1)
     coef, *_ = np.linalg.lstsq(A, np.asarray(p, dtype=np.float64), rcond=None)
     return coef[0] + 1j * coef[1]
+
+
+def pulse_cylinder(x, y, t, xs, ys, a_cyl, amp, w, Zfun=None, xc=0.0, yc=0.0, nw=3000, wmax=None,
+                   nextra=20, scattered_only=False):
+    """App. B: pressure of the Gaussian pulse p0 = amp exp(-b |x - xs|^2),
+    u = v = 0 at t = 0 (b = ln 2 / w^2, rho = c = 1), scattered by a cylinder
+    of radius a_cyl at (xc, yc), at points (x, y) (inside the source radius)
+    and times t.  The initial-value problem equals the causal response to the
+    source p0(x) delta'(t); in the e^{-i w t} convention of App. B its
+    spectrum is, with k = w,
+        P(x, w) = (w / 4) (pi / b) e^{-k^2 / 4b} [H0(k |x - xs|)
+                  + sum_n eps_n H_n(k r_s) S_n(w) H_n(k r) cos(n (th - th_s))],
+        S_n = -(J_n(ka) - i Z J_n'(ka)) / (H_n(ka) - i Z H_n'(ka))  (H = H^(1)),
+    Z(w) = Zfun(w) the impedance in this convention (for the MSD wall
+    R - i (M w - K / w)), None: rigid (S_n = -J_n'/H_n'); and
+    p(x, t) = (1/pi) Re int_0^wmax P(x, w) e^{-i w t} dw by Gauss-Legendre
+    quadrature with nw nodes; wmax defaults to 12 sqrt(b) (the Gaussian factor
+    below 1e-15), modes up to ceil(k a) + nextra."""
+    from scipy.special import hankel1, h1vp, jv, jvp
+    b = np.log(2.0) / w ** 2
+    wmax = 12.0 * np.sqrt(b) if wmax is None else wmax
+    xg, wq = np.polynomial.legendre.leggauss(nw)
+    om = 0.5 * wmax * (xg + 1.0)
+    wq = 0.5 * wmax * wq
+    x = np.atleast_1d(np.asarray(x, dtype=np.float64))
+    y = np.atleast_1d(np.asarray(y, dtype=np.float64))
+    t = np.atleast_1d(np.asarray(t, dtype=np.float64))
+    r = np.hypot(x - xc, y - yc)
+    th = np.arctan2(y - yc, x - xc)
+    rs = np.hypot(xs - xc, ys - yc)
+    ths = np.arctan2(ys - yc, xs - xc)
+    assert np.all(r < rs)
+    k = om
+    C = (om / 4.0) * amp * (np.pi / b) * np.exp(-k * k / (4.0 * b))           # (nw,)
+    P = np.zeros((nw, len(x)), dtype=complex)
+    if not scattered_only:
+        P += hankel1(0, np.outer(k, np.hypot(x - xs, y - ys)))
+    ka = k * a_cyl
+    N = int(np.ceil(ka.max())) + nextra
+    Z = None if Zfun is None else Zfun(om)
+    with np.errstate(all="ignore"):
+        for n in range(N + 1):
+            eps = 1.0 if n == 0 else 2.0
+            if Z is None:
+                S = -jvp(n, ka) / h1vp(n, ka)
+            else:
+                S = -(jv(n, ka) - 1j * Z * jvp(n, ka)) / (hankel1(n, ka) - 1j * Z * h1vp(n, ka))
+            term = (eps * hankel1(n, k * rs) * S)[:, None] * hankel1(n, np.outer(k, r)) * np.cos(n * (th - ths))[None, :]
+            # at low k and high n the factors over- and underflow; the term
+            # there is of order (a^2 / (r r_s))^n, far below rounding
+            P += np.where(np.isfinite(term), term, 0.0)
+    P *= (C * wq)[:, None]
+    # p(x_j, t_i) = (1/pi) Re sum_w P(w, x_j) e^{-i w t_i}
+    E = np.exp(-1j * np.outer(t, om))                                          # (nt, nw)
+    return np.real(E @ P) / np.pi

@@ -293,10 +293,13 @@ def test_float_float_ghost_gather_matches_fp64_gather(case_expr, cuda_device, tm
     summed magnitudes, so the FP32 ghost values they store are equal or one
     unit in the last place apart: after one step the fields agree within a few
     FP32 units of the field's largest value, after 200 steps within 1e-6 of
-    it on the cylinder.  The flat wall meets the radiation band, whose closure
-    amplifies differences at rounding level (its grid-scale modes grow
-    slowly): there the bar after 200 steps is 1e-5, the FP32 parity bar."""
+    it on the cylinder.  The flat wall meets the radiation band, where the
+    closure amplifies differences at rounding level (3e-5 of the field after
+    200 steps without damping): it runs with the absorbing ramp, and its bar
+    after 200 steps is 1e-5, the FP32 parity bar."""
     late = 1e-5 if "flat_wall" in case_expr else 1e-6
+    if "flat_wall" in case_expr:
+        case_expr = "workloads.Case(**dict(vars(%s), sponge=workloads.LONG_RUN_SPONGE))" % case_expr
     for steps, tol in ((1, 2.0 ** -21), (200, late)):
         ff = _run_with_env(tmp_path, "ff%d" % steps, {}, case_expr, steps)
         f64 = _run_with_env(tmp_path, "f64_%d" % steps, {"LEE_GHOST_ARITH": "f64"}, case_expr, steps)
