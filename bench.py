@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lee", choices=["lee", "reference"])
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "cylinder", "free"])
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "cylinder", "free", "flat", "monopole"])
     ap.add_argument("--count", type=int, default=512)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
@@ -93,8 +93,15 @@ def workload_cases(args, rank, accept=None):
             c.wall, c.imp = ("none",), ("rigid",)
             cases.append(c)
         return cases, 0, "wall-free 1024^2 pulses, %d instances (diagnostic)" % len(cases)
+    if args.workload == "flat":
+        c = workloads.flat_wall(128)
+        return [c], 0, "flat impedance wall 128^2 at 30 deg, R=1 M=0.05 K=5 (double pole), no ramp"
+    if args.workload == "monopole":
+        c = workloads.monopole(2048)
+        return [c], 0, ("monopole-cylinder 2048^2, r = 100 cells, source at 300 cells, 20 points per wavelength, "
+                        "R=1 M=0.1 K=10, 256-probe ring, ramp 12")
     c = workloads.cylinder_pulse(1024)
-    return [c], 0, "cylinder pulse 1024^2, r = 50 cells, R=2 M=0.02 K=1"
+    return [c], 0, "cylinder pulse 1024^2, r = 50 cells, R=2 M=0.02 K=1, ramp 12"
 
 
 class ClockSampler:
@@ -230,9 +237,9 @@ def run_serving(args):
         sizes = sorted({c.nx for _, c in trace})
         flat = sum(1 for _, c in trace if c.wall[0] == "line")
         return ("Poisson %.0f/s for %.3f s (seed 24786): %d requests (%d flat walls, %d cylinders), n in %s, "
-                "%d-%d steps, %d draws redrawn (set-up rejected: unstable ADE), absorbing ramp %s" %
+                "%d-%d steps, %d draws redrawn (set-up rejected: unstable ADE), absorbing ramp %s (flat walls %s)" %
                 (rate, duration, len(trace), flat, len(trace) - flat, sizes, min(c.steps for _, c in trace),
-                 max(c.steps for _, c in trace), redrawn, trace[0][1].sponge))
+                 max(c.steps for _, c in trace), redrawn, workloads.LONG_RUN_SPONGE, workloads.WALL_EDGE_SPONGE))
     trace = workloads.serving_trace(rate=args.serve_rate, duration=args.serve_duration, accept=accept)
     out = {"trace": describe(trace, args.serve_rate, args.serve_duration, rejected[0]),
            "budget_bytes": 80 * 10**9}

@@ -23,7 +23,10 @@
  *   1993), the scheme the paper cites for its boundary rows (Sec. 2.2), on
  *   nodes 0..6 from the edge.  Radiation condition of Tam and Webb in the three
  *   outer layers (Secs. 4.1-4.2): dq/dt = -(cos th dq/dx + sin th dq/dy +
- *   q/(2 rho)), polar about the domain centre, no source there.  The paper adds
+ *   q/(2 rho)), polar about the domain centre, no source there; where a wall
+ *   meets the band, a derivative whose 7-node window holds a non-fluid node is
+ *   left out of the condition (its one-sided row would otherwise feed ghost
+ *   values from clouds clipped by the box back into the node).  The paper adds
  *   no damping (Sec. 4.3); an absorbing ramp over the W outer layers (rate
  *   (kappa/h) ((W - d)/W)^2 at distance d from the edge) is available as an
  *   opt-in departure (orc_set_sponge), off by default, for runs longer than
@@ -855,8 +858,20 @@ static void orc_rhs(orc_t *o, double *q[3], const double *X, double sigma, doubl
                 double rx = node_x(o, i) - xc, ry = node_y(o, j) - yc;
                 double rho = sqrt(rx * rx + ry * ry);
                 double ct = rx / rho, st = ry / rho;
-                for (int f = 0; f < 3; f++)
-                    rq[f][s] = -(ct * dx_at(o, q[f], i, j) + st * dy_at(o, q[f], i, j) + q[f][s] / (2.0 * rho));
+                /* where a wall meets the band, a derivative whose stencil
+                 * window holds a non-fluid node is left out of the radiation
+                 * condition (reading for walls that reach the outer boundary) */
+                int wx = 1, wy = 1, lo, hi;
+                footprint(i, nx, o->per_x, &lo, &hi);
+                for (int a = lo; a <= hi; a++) if (o->kind[j * nx + wrap(a, nx)] != 1) wx = 0;
+                footprint(j, ny, o->per_y, &lo, &hi);
+                for (int b = lo; b <= hi; b++) if (o->kind[wrap(b, ny) * nx + i] != 1) wy = 0;
+                for (int f = 0; f < 3; f++) {
+                    double dr = 0.0;
+                    if (wx) dr += ct * dx_at(o, q[f], i, j);
+                    if (wy) dr += st * dy_at(o, q[f], i, j);
+                    rq[f][s] = -(dr + q[f][s] / (2.0 * rho));
+                }
             } else {
                 double src = 0.0;
                 if (samp != 0.0) {

@@ -493,6 +493,7 @@ __device__ __forceinline__ void band_point(const T *__restrict__ gin, const QnSr
     const int sx = band_window(gx, d.nx, d.per_x, tx);
     const int sy = band_window(gy, d.ny, d.per_y, ty);
     T wx[3][7], wy[3][7];
+    bool fx = true, fy = true;                   // every node of the window is fluid
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
         int xk = sx + k, yk = sy + k;
@@ -504,10 +505,15 @@ __device__ __forceinline__ void band_point(const T *__restrict__ gin, const QnSr
             wx[f][k] = gin[f * plane + ox];
             wy[f][k] = gin[f * plane + oy];
         }
+        fx = fx && __ldg(d.mask + ox) == 1;
+        fy = fy && __ldg(d.mask + oy) == 1;
     }
-    const T dpdx = band_deriv<T>(wx[0], tx, inv_h), dpdy = band_deriv<T>(wy[0], ty, inv_h);
-    const T dudx = band_deriv<T>(wx[1], tx, inv_h), dudy = band_deriv<T>(wy[1], ty, inv_h);
-    const T dvdx = band_deriv<T>(wx[2], tx, inv_h), dvdy = band_deriv<T>(wy[2], ty, inv_h);
+    // where a wall meets the band, a derivative whose window holds a non-fluid
+    // node is left out of the radiation condition (its one-sided row would
+    // feed back ghost values extrapolated from clouds clipped by the box)
+    const T dpdx = fx ? band_deriv<T>(wx[0], tx, inv_h) : T(0), dpdy = fy ? band_deriv<T>(wy[0], ty, inv_h) : T(0);
+    const T dudx = fx ? band_deriv<T>(wx[1], tx, inv_h) : T(0), dudy = fy ? band_deriv<T>(wy[1], ty, inv_h) : T(0);
+    const T dvdx = fx ? band_deriv<T>(wx[2], tx, inv_h) : T(0), dvdy = fy ? band_deriv<T>(wy[2], ty, inv_h) : T(0);
     const T rx = T(gx) - (T)d.cx, ryy = T(gy) - (T)d.cy;
     T ct, st, q2;                                                // cos th, sin th, 1 / (2 h rho)
     if constexpr (sizeof(T) == 4) {

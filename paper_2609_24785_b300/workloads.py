@@ -25,6 +25,10 @@ CFL = 0.5
 # damping; the flat-wall workload (400 steps) and the short parity cases run
 # without it.
 LONG_RUN_SPONGE = (12, 0.04)
+# The same ramp ten times stronger for straight walls that meet the outer band
+# and run thousands of steps (serving): it removes the growing modes of the
+# edge nodes next to the wall that the weaker ramp leaves (spectral study).
+WALL_EDGE_SPONGE = (12, 0.4)
 
 
 @dataclass
@@ -135,13 +139,15 @@ SERVE_SIZES = (256, 384, 512, 768, 1024, 1536, 2048)
 
 
 def serving_trace(rate=200.0, duration=1.0, seed=24786, accept=None, sizes=SERVE_SIZES,
-                  steps_range=(1000, 10000), sponge=LONG_RUN_SPONGE) -> List[Tuple[float, Case]]:
+                  steps_range=(1000, 10000), sponge=LONG_RUN_SPONGE,
+                  wall_sponge=WALL_EDGE_SPONGE) -> List[Tuple[float, Case]]:
     """Poisson arrivals (mean `rate` per second over `duration` seconds) of mixed
     solves: half flat walls through the centre at an angle U[0, 60] deg, half
     cylinders of radius U[0.05, 0.15] n; pulse of half-width 4 cells at a
     uniform position at least 20 cells from the wall and the edges; R, M, K as
-    in the sweep; steps uniform in steps_range; the long-run absorbing ramp
-    (flat walls meet the radiation band, and runs last up to 10000 steps)."""
+    in the sweep; steps uniform in steps_range; the long-run absorbing ramp for
+    cylinders and the stronger one for flat walls, which meet the outer band
+    (runs last up to 10000 steps)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     t, out = 0.0, []
     while True:
@@ -170,7 +176,8 @@ def serving_trace(rate=200.0, duration=1.0, seed=24786, accept=None, sizes=SERVE
                 pos = np.array(c) + d * H * np.array([math.cos(ang), math.sin(ang)])
             case = Case("serve_%d_n%d" % (len(out), n), n, n, wall=wall, imp=("msd", R, M, K),
                         init=("pulse", pos[0], pos[1], 1.0, 4 * H),
-                        probes=np.array([[pos[0], pos[1]]]), steps=steps, sponge=sponge)
+                        probes=np.array([[pos[0], pos[1]]]), steps=steps,
+                        sponge=wall_sponge if wall[0] == "line" else sponge)
             if accept is None or accept(case):
                 break
         out.append((t, case))

@@ -22,15 +22,13 @@ def _mixed_cases(k=6):
             wall = ("cyl", c[0], c[1], 0.12 * n * H)
             pos = (c[0] + 0.3 * n * H, c[1] + 0.05 * n * H)
         else:
-            # walls at 0, 10, 20 degrees: a straight wall meets the outer
-            # radiation band, and at some angles and offsets the edge node next
-            # to it carries a fast-growing mode (see the stability study)
-            th = math.radians(5.0 * i)
+            th = math.radians(10.0 * i)
             wall = ("line", c[0] + 0.37 * H, c[1], th)
             pos = (c[0] - 0.25 * n * H * math.sin(th), c[1] + 0.25 * n * H * math.cos(th))
         out.append(workloads.Case("mix%d" % i, n, n, wall=wall, imp=("msd", 0.5 + 0.3 * i, 0.02, 2.0 + i),
                                   init=("pulse", pos[0], pos[1], 1.0, 4 * H), probes=np.array([pos]),
-                                  steps=150 + 97 * i, sponge=workloads.LONG_RUN_SPONGE))
+                                  steps=150 + 97 * i,
+                                  sponge=workloads.WALL_EDGE_SPONGE if i % 2 == 0 else workloads.LONG_RUN_SPONGE))
     return out
 
 
