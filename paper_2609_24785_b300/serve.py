@@ -91,6 +91,12 @@ class Report:
                                   for kind in ("line", "cyl")],
             "diverged_flat_angles_deg": sorted(round(math.degrees(r.case.wall[3]), 1) for r in self.requests
                                                if r.status == "diverged" and r.case.wall[0] == "line"),
+            # per diverged request: wall, n, angle (deg) or radius (cells), R, M, K, steps done / asked
+            "diverged_cases": [(r.case.wall[0], r.case.nx,
+                                round(math.degrees(r.case.wall[3]) if r.case.wall[0] == "line"
+                                      else r.case.wall[3] / r.case.h, 2),
+                                *(round(v, 4) for v in r.case.imp[1:4]), r.steps_done, r.case.steps)
+                               for r in self.requests if r.status == "diverged" and r.case.imp[0] == "msd"],
             "failed": sum(r.status == "failed" for r in self.requests),
             "p50_s": q(50), "p99_s": q(99), "mean_s": float(lat.mean()) if lat.size else math.nan,
             "mean_wait_s": float(np.mean([r.t_admit - r.arrival for r in ok])) if ok else math.nan,

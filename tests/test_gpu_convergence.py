@@ -1,10 +1,17 @@
-"""Convergence of the whole solver on the GPU (FP64 bulk): a pulse reflected by
-a cylinder, the same physical problem on 256^2, 512^2 and 1024^2 grids,
-compared with a 2048^2 run at the same physical times and probe positions.
-The paper measures about 3 on the impedance cylinder (Sec. 4).  The errors
-must fall at every refinement and the mean order over 256 -> 1024 must be at
-least 3.  Measured on a B300: rigid 5.0e-3, 2.0e-4, 4.2e-5 (orders 4.7, 2.2,
-mean 3.4); impedance 5.4e-3, 1.9e-4, 2.8e-5 (4.9, 2.7, mean 3.8)."""
+"""Convergence of the whole solver on the GPU (FP64 bulk).
+
+Cylinder self-convergence: a pulse reflected by a cylinder, the same physical
+problem on 256^2, 512^2 and 1024^2 grids, compared with a 2048^2 run at the
+same physical times and probe positions.  Measured on a B300: rigid 5.0e-3,
+2.0e-4, 4.2e-5 (orders 4.7, 2.2); impedance 5.4e-3, 1.9e-4, 2.8e-5 (4.9, 2.7).
+The last order depends on the cylinder's sub-cell position (rigid 2.2-2.9,
+impedance 2.7-3.7 over four centre offsets; energy conserved to 1e-5 on every
+grid): a geometry-dependent error component of the ghost configuration, not
+the reference's own error.  Asserted per refinement: first order >= 4, second
+>= 2, mean >= 3.
+
+Against exact and semi-analytic references: the paper's Sec. 4.1 flat wall
+(App. A) and Sec. 4.2 pulse-cylinder (App. B), and the Fig. 8b R sweep."""
 import math
 
 import numpy as np
@@ -57,6 +64,7 @@ def test_cylinder_pulse_converges(rigid, cuda_device):
     print("%s: relative probe errors %s, orders %s, mean %.2f" % (
         "rigid" if rigid else "impedance", ["%.2e" % e for e in errs], ["%.2f" % o for o in orders], mean))
     assert errs[0] > errs[1] > errs[2]
+    assert orders[0] >= 4.0 and orders[1] >= 2.0, (errs, orders)
     assert mean >= 3.0, (errs, orders)
 
 
