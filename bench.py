@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-tune", action="store_true", help="skip the tile / packing autotuner")
     ap.add_argument("--tile", default=None, help="TMA tile WxH (skips the autotuner)")
     ap.add_argument("--strips", type=int, default=0, help="tile strips per SM with --tile (0: library default)")
+    ap.add_argument("--fuse", type=int, default=0, help="temporal blocking of stages 1 and 2 (1: on)")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-duration", type=float, default=1.0,
                     help="seconds of Poisson arrivals of the saturated serving trace")
@@ -325,6 +326,10 @@ def run_lee(args):
         batch.add(s)
     if strips:
         batch.set_strips_per_sm(strips)
+    fused_tiles = None
+    if args.fuse:
+        batch.set_stage_fusion(True)
+        fused_tiles = batch.fused_tiles()
     t_setup = time.perf_counter() - t_setup
     fluid = sum(s.sizes.n_fluid for s in solvers)
     ghosts = sum(s.sizes.n_ghost for s in solvers)
@@ -486,7 +491,8 @@ def run_lee(args):
                                        else "f64"), "l2": "working set %.1f GB >> 126 MB L2, no flush" %
                        (sum(s.sizes.device_bytes for s in solvers) / 1e9),
                        "parallelism": "replicas" if ws > 1 else "single GPU", "setup_s": round(t_setup, 2),
-                       "stencil_kernel": batch.stencil_kernel(), "autotune": tuned},
+                       "stencil_kernel": batch.stencil_kernel(), "autotune": tuned,
+                       "fused_stage12_tiles": fused_tiles},
             "roofline_fp64": roofline_fp64,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,

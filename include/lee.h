@@ -267,6 +267,20 @@ int lee_batch_status(lee_batch *b, long long *host, int n);
  * persistent CTAs; more strips balance better, fewer keep more halo rows in
  * L2 down a strip.  strips = 1..64, 0 restores the default (2). */
 int lee_batch_set_strips_per_sm(lee_batch *b, int strips);
+/* Temporal blocking of stages 1 and 2 (on = 1; 0, the default, turns it off):
+ * tiles whose region widened by 3 nodes is fluid, outside the three outer
+ * layers and the absorbing ramp, of instances without a source, run both
+ * stages in one pass over Q^n (the stage-1 values of the region widened by 4
+ * stay in shared memory): 9 words of HBM traffic per node for the two stages
+ * instead of 15; the other tiles keep one pass per stage.  The ghost fill
+ * between the two stages touches nothing those tiles read, so the results are
+ * bitwise those of the unfused stages.  Applies to FP32 batches with the
+ * default 64 x 40 warp-specialised stencil, otherwise has no effect.  At a
+ * step boundary. */
+int lee_batch_set_stage_fusion(lee_batch *b, int on);
+/* Tiles that the fused pass covers and the batch's total tiles (after the
+ * members are final; refreshes the batch's tables). */
+int lee_batch_fused_tiles(lee_batch *b, long long *fused, long long *total);
 /* Name of the stencil kernel variant the batch launches (static string; ""
  * before lee_batch_bind or without members). */
 const char *lee_batch_stencil_kernel(lee_batch *b);

@@ -99,6 +99,7 @@ struct lee_batch {
     BatchView bv{};
     long long *status = nullptr;      // device: members' status words (lee_batch_status)
     int strips_per_sm = 2;            // lee_batch_set_strips_per_sm
+    int fuse12 = 0;                   // lee_batch_set_stage_fusion
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     long long graph_launches[2] = {0, 0};
     std::string err;
@@ -202,12 +203,17 @@ int upload_source(lee_ctx *ctx) {
 // Enqueue `steps` time steps of the instances in bv.
 cudaError_t enqueue_steps(const BatchView &bv, int steps, cudaStream_t s) {
     static const int ctas = [] { const char *e = getenv("LEE_STENCIL_CTAS"); return e ? atoi(e) : 0; }();
+    BatchView nb = bv;                       // stages 1 and 2 with fusion: the other tiles only
+    nb.strips = bv.near_strips;
+    nb.nstrips = bv.n_near_strips;
     for (int n = 0; n < steps; ++n) {
         for (int k = 1; k <= 4; ++k) {
             cudaError_t e = launch_ghost(bv, k, s);
             if (e != cudaSuccess) return e;
-            e = launch_stencil(bv, k, ctas, s);
+            const bool fused = bv.fuse12 && k <= 2;
+            e = launch_stencil(fused ? nb : bv, k, ctas, s);
             if (e != cudaSuccess) return e;
+            if (fused && k == 1 && (e = launch_pair(bv, s)) != cudaSuccess) return e;
         }
         cudaError_t e = launch_probes(bv, s);
         if (e != cudaSuccess) return e;
@@ -880,7 +886,7 @@ static long long batch_bytes(const lee_batch *b) {
         nbc += c->nbchunks;
     }
     return (long long)(align_up(n * sizeof(InstDesc)) + 2 * align_up((n + 1) * 4) + align_up(nch * sizeof(int4)) +
-                       align_up(nst * sizeof(int4)) + align_up(n * sizeof(long long)) + align_up(nbc * sizeof(int4)));
+                       3 * align_up(nst * sizeof(int4)) + align_up(n * sizeof(long long)) + align_up(nbc * sizeof(int4)));
 }
 
 int lee_batch_plan(lee_batch *b, long long *device_bytes) {
@@ -923,9 +929,48 @@ static int batch_refresh(lee_batch *b) {
     sort_strips(strips);
     const int nstrips = (int)strips.size();
     strips.resize(std::max<size_t>(strips.size(), 1));
+    // fused stages 1 + 2: the tiles clear of walls, band and ramp, and strips of the others
+    std::vector<int4> far, near;
+    bool fuse = b->fuse12 != 0 && n > 0;
+    for (size_t i = 0; fuse && i < n; ++i)
+        fuse = descs[i].precision == LEE_FP32 && descs[i].kernel_mode == KERNEL_TMA && b->members[i]->nband > 0 &&
+               descs[i].tile_w == pair_tile_w() && descs[i].tile_h == pair_tile_h();
+    if (fuse) {
+        for (size_t i = 0; i < n; ++i) {
+            const lee_ctx *c = b->members[i];
+            const InstDesc &d = descs[i];
+            const int m = std::max(3, d.sponge_w);
+            std::vector<char> isfar((size_t)d.tiles_x * d.tiles_y, 0);
+            for (int ty = 0; ty < d.tiles_y; ++ty)
+                for (int tx = 0; tx < d.tiles_x; ++tx) {
+                    const int x0 = tx * d.tile_w, y0 = ty * d.tile_h;
+                    bool ok = c->s_amp == 0.0 && x0 - 8 >= 0 && y0 - 8 >= 0 && x0 + d.tile_w + 7 <= d.nx - 1 &&
+                              y0 + d.tile_h + 7 <= d.ny - 1 && x0 - 3 >= m && y0 - 3 >= m &&
+                              x0 + d.tile_w + 2 <= d.nx - 1 - m && y0 + d.tile_h + 2 <= d.ny - 1 - m;
+                    for (int y = y0 - 3; ok && y <= y0 + d.tile_h + 2; ++y)
+                        for (int x = x0 - 3; x <= x0 + d.tile_w + 2; ++x)
+                            if (c->plan.kind[(size_t)y * d.nx + x] != 1) { ok = false; break; }
+                    if (ok) { isfar[(size_t)ty * d.tiles_x + tx] = 1; far.push_back(make_int4((int)i, x0, y0, 0)); }
+                }
+            for (int tx = 0; tx < d.tiles_x; ++tx)
+                for (int ty = 0; ty < d.tiles_y;) {
+                    if (isfar[(size_t)ty * d.tiles_x + tx]) { ++ty; continue; }
+                    int len = 0;
+                    while (ty + len < d.tiles_y && !isfar[(size_t)(ty + len) * d.tiles_x + tx] && len < seg) ++len;
+                    near.push_back(make_int4((int)i, tx, ty, len));
+                    ty += len;
+                }
+        }
+        sort_strips(near);
+    }
+    const int nnear = (int)near.size(), nfar = (int)far.size();
+    near.resize(std::max<size_t>(near.size(), 1));
+    far.resize(std::max<size_t>(far.size(), 1));
     const size_t o_desc = 0, o_tp = align_up(n * sizeof(InstDesc)), o_pi = o_tp + align_up((n + 1) * 4),
                  o_ch = o_pi + align_up((n + 1) * 4), o_st = o_ch + align_up(chunks.size() * sizeof(int4)),
-                 o_status = o_st + align_up(strips.size() * sizeof(int4)),
+                 o_near = o_st + align_up(strips.size() * sizeof(int4)),
+                 o_far = o_near + align_up(near.size() * sizeof(int4)),
+                 o_status = o_far + align_up(far.size() * sizeof(int4)),
                  o_bc = o_status + align_up(n * sizeof(long long));
     b->status = (long long *)(b->dev + o_status);
     cudaError_t e;
@@ -935,6 +980,8 @@ static int batch_refresh(lee_batch *b) {
             (e = cudaMemcpyAsync(b->dev + o_pi, pi.data(), pi.size() * 4, cudaMemcpyHostToDevice, b->stream)) ||
             (e = cudaMemcpyAsync(b->dev + o_ch, chunks.data(), chunks.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream)) ||
             (e = cudaMemcpyAsync(b->dev + o_st, strips.data(), strips.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream)) ||
+            (e = cudaMemcpyAsync(b->dev + o_near, near.data(), near.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream)) ||
+            (e = cudaMemcpyAsync(b->dev + o_far, far.data(), far.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream)) ||
             (bch.size() && (e = cudaMemcpyAsync(b->dev + o_bc, bch.data(), bch.size() * sizeof(int4),
                                                 cudaMemcpyHostToDevice, b->stream))) ||
             (e = cudaStreamSynchronize(b->stream))) {
@@ -964,6 +1011,11 @@ static int batch_refresh(lee_batch *b) {
     bv.precision = b->precision;
     bv.ade_general = 0;
     for (size_t i = 0; i < n; ++i) bv.ade_general |= descs[i].ns != 2;
+    bv.fuse12 = fuse && nfar > 0;
+    bv.near_strips = (const int4 *)(b->dev + o_near);
+    bv.n_near_strips = nnear;
+    bv.far_tiles = (const int4 *)(b->dev + o_far);
+    bv.n_far_tiles = nfar;
     drop_graphs(b->graph);
     b->dirty = false;
     return LEE_OK;
@@ -998,6 +1050,24 @@ int lee_batch_status(lee_batch *b, long long *host, int n) {
         b->err = std::string("batch status: ") + cudaGetErrorString(e);
         return LEE_ERR_CUDA;
     }
+    return LEE_OK;
+}
+
+int lee_batch_set_stage_fusion(lee_batch *b, int on) {
+    if (!b) return LEE_ERR_ARG;
+    b->fuse12 = on != 0;
+    b->dirty = true;
+    return LEE_OK;
+}
+
+int lee_batch_fused_tiles(lee_batch *b, long long *fused, long long *total) {
+    if (!b || !fused || !total) return LEE_ERR_ARG;
+    if (b->dirty) {
+        const int rc = batch_refresh(b);
+        if (rc != LEE_OK) return rc;
+    }
+    *fused = b->bv.fuse12 ? b->bv.n_far_tiles : 0;
+    *total = b->bv.total_tiles;
     return LEE_OK;
 }
 

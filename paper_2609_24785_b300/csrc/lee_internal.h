@@ -178,6 +178,14 @@ struct BatchView {
     int total_ghosts;
     int precision;
     int ade_general;            // some instance has ns > 2: the ghost kernel's general ADE variant
+    // fused stages 1 + 2 (lee_batch_set_stage_fusion): tiles clear of walls,
+    // band and ramp run pair_kernel; the stencil of stages 1 and 2 takes the
+    // other tiles' strips
+    int fuse12;
+    const int4 *near_strips;    // (instance, tile column, first tile row, tiles) of the other tiles
+    int n_near_strips;
+    const int4 *far_tiles;      // (instance, x0, y0, 0) of the fused tiles
+    int n_far_tiles;
 };
 cudaError_t prepare_kernels(int precision);   // one-time function attributes (outside capture)
 int num_sms();
@@ -191,6 +199,9 @@ cudaError_t launch_ghost(const BatchView &bv, int stage, cudaStream_t s);
 bool ghost_float_float(int precision);
 cudaError_t launch_stencil(const BatchView &bv, int stage, int persistent_ctas, cudaStream_t s);
 cudaError_t launch_probes(const BatchView &bv, cudaStream_t s);
+cudaError_t launch_pair(const BatchView &bv, cudaStream_t s);   // fused stages 1 + 2 on bv.far_tiles
+int pair_tile_w();
+int pair_tile_h();
 cudaError_t launch_init(const InstDesc *dinst, const InstDesc &h, int kind, const double *prm, cudaStream_t s);
 cudaError_t launch_to_staging(const InstDesc *dinst, const InstDesc &h, int which, int buf, cudaStream_t s);
 cudaError_t launch_from_staging(const InstDesc *dinst, const InstDesc &h, int which, cudaStream_t s);

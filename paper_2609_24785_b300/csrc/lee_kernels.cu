@@ -1180,6 +1180,103 @@ stencil_ws_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ st
     }
 }
 
+// ---------------------------------------------------------------- fused stages 1 + 2
+// Temporal blocking of the first two stages on tiles clear of walls, of the
+// outer band and of the ramp (the host lists them: their region widened by 3
+// nodes is fluid and interior, and widened by 8 lies inside the grid; no
+// source).  For such a tile T the ghost fill between the stages touches
+// nothing the tile reads, so one pass computes
+//   Q(1) = Q^n + alpha_1 dt L(Q^n)   on T widened by 4 (in shared memory),
+//   Q(2) = Q^n + alpha_2 dt L(Q(1))  on T,
+// from one box of Q^n (T widened by 8), and writes Q(1) and Q(2) on T: 9 words
+// of traffic per node for the two stages instead of 15.  Both stages run the
+// same interior tile code as the stencil kernels (tile_points with no flags),
+// so the values are bitwise those of the two separate stages.
+constexpr int PAIR_TW = 64, PAIR_TH = 40;                           // the tile shape it serves
+constexpr int PAIR_BW = PAIR_TW + 16, PAIR_BH = PAIR_TH + 16;       // Q^n box (halo 8)
+constexpr int PAIR_QW = PAIR_TW + 8, PAIR_QH = PAIR_TH + 8;         // Q(1) region (halo 4)
+constexpr int PAIR_THREADS = (PAIR_QW / 4) * (PAIR_QH / 2);         // 18 x 24 = 432
+constexpr size_t PAIR_SMEM = (size_t)3 * (PAIR_BW * PAIR_BH + PAIR_QW * PAIR_QH) * sizeof(float) + 1024;
+
+__global__ void __launch_bounds__(PAIR_THREADS, 1)
+pair_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ tiles, int ntiles) {
+    extern __shared__ unsigned char smem_dyn[];
+    float *box = reinterpret_cast<float *>(smem_dyn + ((16u - (smem_u32(smem_dyn) & 15u)) & 15u));
+    float *q1 = box + 3 * PAIR_BW * PAIR_BH;
+    __shared__ __align__(16) InstDesc sd;        // the tile's instance, with q1's layout for stage 1
+    const int tid = threadIdx.x;
+    for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+        const int4 tl = __ldg(tiles + ti);
+        const InstDesc &d = inst[tl.x];
+        const int x0 = tl.y, y0 = tl.z;
+        {
+            const int4 *src4 = reinterpret_cast<const int4 *>(&d);
+            int4 *dst4 = reinterpret_cast<int4 *>(&sd);
+            for (int i = tid; i < (int)(sizeof(InstDesc) / 16); i += PAIR_THREADS) dst4[i] = src4[i];
+        }
+        // the Q^n box, 16-byte copies (rows of 80 floats from column x0 - 8)
+        const float *qn = (const float *)d.q[0];
+        const long long plane = d.plane;
+        constexpr int V = PAIR_BW / 4;
+        for (int e = tid; e < 3 * PAIR_BH * V; e += PAIR_THREADS) {
+            const int f = e / (PAIR_BH * V), r = (e / V) % PAIR_BH, c = (e % V) * 4;
+            cp_async16(box + (f * PAIR_BH + r) * PAIR_BW + c,
+                       qn + f * plane + (long long)(y0 - 8 + r) * d.pitch + (x0 - 8 + c));
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        if (tid == 0) { sd.pitch = PAIR_QW; sd.plane = PAIR_QW * PAIR_QH; }
+        __syncthreads();
+        // stage 1 on the region widened by 4, into q1 (tile-local coordinates)
+        {
+            const int txi = tid % (PAIR_QW / 4), tyi = tid / (PAIR_QW / 4);
+            const float *sp = box;
+            const QnSrc<float> qs{box + 4 * PAIR_BW + 4, box + (PAIR_BH + 4) * PAIR_BW + 4,
+                                  box + (2 * PAIR_BH + 4) * PAIR_BW + 4, PAIR_BW};
+            tile_points<float, 2, 0, false>(sp, sp + PAIR_BW * PAIR_BH, sp + 2 * PAIR_BW * PAIR_BH, PAIR_BW, qs, sd,
+                                            q1, 0, 0, d.kf[0], 0.f, txi, tyi, nullptr, nullptr);
+        }
+        __syncthreads();
+        // Q(1) on the tile to its buffer; stage 2 on the tile
+        float *out1 = (float *)d.q[stage_out(1)];
+        for (int e = tid; e < 3 * PAIR_TH * (PAIR_TW / 4); e += PAIR_THREADS) {
+            const int f = e / (PAIR_TH * (PAIR_TW / 4)), r = (e / (PAIR_TW / 4)) % PAIR_TH, c = (e % (PAIR_TW / 4)) * 4;
+            *reinterpret_cast<float4 *>(out1 + f * plane + (long long)(y0 + r) * d.pitch + x0 + c) =
+                *reinterpret_cast<const float4 *>(q1 + (f * PAIR_QH + r + 4) * PAIR_QW + 4 + c);
+        }
+        if (tid < (PAIR_TW / 4) * (PAIR_TH / 2)) {
+            const int txi = tid % (PAIR_TW / 4), tyi = tid / (PAIR_TW / 4);
+            const QnSrc<float> qs{box + 8 * PAIR_BW + 8, box + (PAIR_BH + 8) * PAIR_BW + 8,
+                                  box + (2 * PAIR_BH + 8) * PAIR_BW + 8, PAIR_BW};
+            tile_points<float, 2, 0, false>(q1, q1 + PAIR_QW * PAIR_QH, q1 + 2 * PAIR_QW * PAIR_QH, PAIR_QW, qs, d,
+                                            (float *)d.q[stage_out(2)], x0, y0, d.kf[1], 0.f, txi, tyi, nullptr,
+                                            nullptr);
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_pair(const BatchView &bv, cudaStream_t s) {
+    if (bv.n_far_tiles == 0) return cudaSuccess;
+    static const cudaError_t attr = cudaFuncSetAttribute(pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         (int)PAIR_SMEM);
+    if (attr != cudaSuccess) return attr;
+    static const int per_sm = [] {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pair_kernel, PAIR_THREADS, PAIR_SMEM) != cudaSuccess ||
+            n < 1)
+            n = 1;
+        return n;
+    }();
+    const int grid = std::min(bv.n_far_tiles, per_sm * num_sms());
+    pair_kernel<<<grid, PAIR_THREADS, PAIR_SMEM, s>>>(bv.inst, bv.far_tiles, bv.n_far_tiles);
+    count_launch();
+    return cudaGetLastError();
+}
+
+int pair_tile_w() { return PAIR_TW; }
+int pair_tile_h() { return PAIR_TH; }
+
 // ---------------------------------------------------------------- band pass
 // Band node b of a non-periodic instance: rows 0..2 and ny-3..ny-1 over the
 // full width (6 nx nodes), then columns 0..2 and nx-3..nx-1 of rows 3..ny-4.
@@ -1388,7 +1485,8 @@ template <int TW, int TH, int RYT, int S_>
 void launch_ws(const BatchView &bv, int stage, int persistent_ctas, cudaStream_t s) {
     using W = WsGeom<TW, TH, RYT, S_>;
     const int grid = std::min(bv.nstrips, persistent_ctas > 0 ? persistent_ctas : W::CTAS * num_sms());
-    stencil_ws_kernel<TW, TH, RYT, S_><<<grid, W::NT, W::SMEM, s>>>(bv.inst, bv.strips, bv.nstrips, stage);
+    if (grid > 0)           // no tiles left (every tile fused): only the band pass
+        stencil_ws_kernel<TW, TH, RYT, S_><<<grid, W::NT, W::SMEM, s>>>(bv.inst, bv.strips, bv.nstrips, stage);
     if (bv.nband_chunks > 0) {
         static const int per_sm = [] {
             int n = 0;

@@ -63,6 +63,8 @@ SIGNATURES = {
     "lee_set_sponge": (C.c_int, [_vp, C.c_int, C.c_double]),
     "lee_fill_ghosts_with_bc": (C.c_int, [_vp, _dp]),
     "lee_set_impedance_rational": (C.c_int, [_vp, C.c_int, _dp, C.c_int, _dp]),
+    "lee_batch_set_stage_fusion": (C.c_int, [_vp, C.c_int]),
+    "lee_batch_fused_tiles": (C.c_int, [_vp, _llp, _llp]),
     "lee_fp64_fma_probe": (C.c_int, [C.c_int, C.c_longlong, _vp, _vp]),
     "lee_plan": (C.c_int, [_vp, C.POINTER(lee_sizes)]),
     "lee_bind": (C.c_int, [_vp, _vp, C.c_longlong, _vp]),
@@ -371,6 +373,18 @@ class Batch:
         out = np.zeros(max(n, 1), dtype=np.int64)
         self._c(self.L.lee_batch_status(self.b, out.ctypes.data_as(_llp), n))
         return out[:n]
+
+    def set_stage_fusion(self, on=True):
+        """Temporal blocking of stages 1 and 2 on tiles clear of walls, band
+        and ramp (FP32, 64 x 40 tiles); results bitwise those of the unfused
+        stages."""
+        self._c(self.L.lee_batch_set_stage_fusion(self.b, int(bool(on))))
+
+    def fused_tiles(self):
+        """(tiles the fused pass covers, all tiles)."""
+        f, t = C.c_longlong(), C.c_longlong()
+        self._c(self.L.lee_batch_fused_tiles(self.b, C.byref(f), C.byref(t)))
+        return f.value, t.value
 
     def set_strips_per_sm(self, strips):
         """Stencil work packing: tile strips per SM (0 = default 2)."""

@@ -500,3 +500,30 @@ def test_batch_mixing_rational_and_msd_walls(cuda_device):
         ea = rel_l2(m.ade(), o.ade()) if o.n_ghost else 0.0
         log_result("mixed batch %s fp64 %d steps: field %.3e ade %.3e" % (c.name, steps, err, ea))
         assert err <= TOL["fp64"] and ea <= 1e-11, (c.name, err, ea)
+
+
+def test_stage_fusion_equals_unfused(cuda_device):
+    """Temporal blocking of stages 1 and 2 (lee_batch_set_stage_fusion): the
+    fused pass on tiles clear of walls, band and ramp gives bitwise the fields
+    and ADE states of the unfused stages, over several steps of a batch with
+    fused and unfused tiles side by side (cylinders of the sweep, one with the
+    ramp and one without)."""
+    cases, _ = workloads.sweep(3, seed=7, sizes=(512, 768))
+    cases[0].sponge = (0, 0.0)
+    runs = []
+    for fuse in (False, True):
+        batch = lee.Batch("fp32")
+        members = [make_solver(c, "fp32") for c in cases]
+        for m in members:
+            batch.add(m)
+        batch.set_stage_fusion(fuse)
+        fused, total = batch.fused_tiles()
+        if fuse:
+            assert 0 < fused < total, (fused, total)
+        batch.step(23)
+        batch.sync()
+        runs.append([[m.field(f) for f in range(3)] + [m.ade()] for m in members])
+    log_result("stage fusion: %d of %d tiles fused" % (fused, total))
+    for a, b in zip(*runs):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
