@@ -1198,7 +1198,7 @@ constexpr int PAIR_QW = PAIR_TW + 8, PAIR_QH = PAIR_TH + 8;         // Q(1) regi
 constexpr int PAIR_THREADS = (PAIR_QW / 4) * (PAIR_QH / 2);         // 18 x 24 = 432
 constexpr size_t PAIR_SMEM = (size_t)3 * (PAIR_BW * PAIR_BH + PAIR_QW * PAIR_QH) * sizeof(float) + 1024;
 
-__global__ void __launch_bounds__(PAIR_THREADS, 1)
+__global__ void __launch_bounds__(PAIR_THREADS, 2)
 pair_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ tiles, int ntiles) {
     extern __shared__ unsigned char smem_dyn[];
     float *box = reinterpret_cast<float *>(smem_dyn + ((16u - (smem_u32(smem_dyn) & 15u)) & 15u));
