@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--tile", default=None, help="TMA tile WxH (skips the autotuner)")
     ap.add_argument("--strips", type=int, default=0, help="tile strips per SM with --tile (0: library default)")
     ap.add_argument("--fuse", type=int, default=0, help="temporal blocking of stages 1 and 2 (1: on)")
+    ap.add_argument("--band-tile", type=int, default=-1,
+                    help="stages (bit k) whose band nodes the stencil updates in its band tiles (-1: default)")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-duration", type=float, default=1.0,
                     help="seconds of Poisson arrivals of the saturated serving trace")
@@ -329,6 +331,8 @@ def run_lee(args):
     fused_tiles = None
     if args.fuse:
         batch.set_stage_fusion(True)
+    if args.band_tile >= 0:
+        batch.set_band_in_tile(args.band_tile)
         fused_tiles = batch.fused_tiles()
     t_setup = time.perf_counter() - t_setup
     fluid = sum(s.sizes.n_fluid for s in solvers)
@@ -394,7 +398,9 @@ def run_lee(args):
     achieved = alg_bytes / (st_ms / 1e3) / 1e9
     traffic = None
     kname = batch.stencil_kernel()
-    kname += (" + band_kernel" if kname.startswith("stencil_ws") else "") + " stage 2"
+    if kname.startswith("stencil_ws"):
+        kname += " + band in tile" if (batch.band_in_tile() >> 2) & 1 else " + band_kernel"
+    kname += " stage 2"
     tf = os.path.join(ROOT, "profiles", "stencil_traffic.json")
     if os.path.exists(tf):
         try:
@@ -492,7 +498,7 @@ def run_lee(args):
                        (sum(s.sizes.device_bytes for s in solvers) / 1e9),
                        "parallelism": "replicas" if ws > 1 else "single GPU", "setup_s": round(t_setup, 2),
                        "stencil_kernel": batch.stencil_kernel(), "autotune": tuned,
-                       "fused_stage12_tiles": fused_tiles},
+                       "fused_stage12_tiles": fused_tiles, "band_in_tile_stages": batch.band_in_tile()},
             "roofline_fp64": roofline_fp64,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,

@@ -278,6 +278,20 @@ int lee_batch_set_strips_per_sm(lee_batch *b, int strips);
  * default 64 x 40 warp-specialised stencil, otherwise has no effect.  At a
  * step boundary. */
 int lee_batch_set_stage_fusion(lee_batch *b, int on);
+/* Where the band nodes (the three outer layers: one-sided DRP rows, Tam-Webb
+ * radiation condition, Sec. 2.2 and Sec. 4.1) of an FP32 batch on the
+ * warp-specialised stencil are updated, per stage: bit k of stage_mask (k =
+ * 2..4) set = inside the stencil's band tiles, from the tile's shared-memory
+ * box, stored with the tile's other nodes; clear = by a separate band pass
+ * over the global planes after the stencil (stage 1 always: its shared copy
+ * of Q^n is the box itself).  Both give bitwise the same values; the
+ * separate pass is the faster on large batches.  -1 restores the default (0:
+ * the separate pass in every stage; the environment variable LEE_BAND_TILE, a
+ * bit mask, overrides it).  LEE_ERR_ARG for bits outside 2..4.  At a step
+ * boundary; no effect on other kernels. */
+int lee_batch_set_band_in_tile(lee_batch *b, int stage_mask);
+/* The stage mask in effect (see lee_batch_set_band_in_tile). */
+int lee_batch_band_in_tile(lee_batch *b, int *stage_mask);
 /* Tiles that the fused pass covers and the batch's total tiles (after the
  * members are final; refreshes the batch's tables). */
 int lee_batch_fused_tiles(lee_batch *b, long long *fused, long long *total);

@@ -100,6 +100,7 @@ struct lee_batch {
     long long *status = nullptr;      // device: members' status words (lee_batch_status)
     int strips_per_sm = 2;            // lee_batch_set_strips_per_sm
     int fuse12 = 0;                   // lee_batch_set_stage_fusion
+    int band_tile = -1;               // lee_batch_set_band_in_tile (-1: default_band_tile_stages())
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     long long graph_launches[2] = {0, 0};
     std::string err;
@@ -288,6 +289,7 @@ BatchView single_view(lee_ctx *c) {
     bv.total_ghosts = c->hd.ng;
     bv.precision = c->g.precision;
     bv.ade_general = c->hd.ns != 2;
+    bv.band_tile = default_band_tile_stages();
     return bv;
 }
 
@@ -1012,6 +1014,7 @@ static int batch_refresh(lee_batch *b) {
     bv.ade_general = 0;
     for (size_t i = 0; i < n; ++i) bv.ade_general |= descs[i].ns != 2;
     bv.fuse12 = fuse && nfar > 0;
+    bv.band_tile = b->band_tile < 0 ? default_band_tile_stages() : b->band_tile;
     bv.near_strips = (const int4 *)(b->dev + o_near);
     bv.n_near_strips = nnear;
     bv.far_tiles = (const int4 *)(b->dev + o_far);
@@ -1057,6 +1060,19 @@ int lee_batch_set_stage_fusion(lee_batch *b, int on) {
     if (!b) return LEE_ERR_ARG;
     b->fuse12 = on != 0;
     b->dirty = true;
+    return LEE_OK;
+}
+
+int lee_batch_set_band_in_tile(lee_batch *b, int stage_mask) {
+    if (!b || stage_mask < -1 || (stage_mask > 0 && (stage_mask & ~28))) return LEE_ERR_ARG;
+    b->band_tile = stage_mask;
+    b->dirty = true;
+    return LEE_OK;
+}
+
+int lee_batch_band_in_tile(lee_batch *b, int *stage_mask) {
+    if (!b || !stage_mask) return LEE_ERR_ARG;
+    *stage_mask = b->band_tile < 0 ? default_band_tile_stages() : b->band_tile;
     return LEE_OK;
 }
 

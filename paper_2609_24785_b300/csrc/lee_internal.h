@@ -36,6 +36,7 @@ constexpr unsigned long long STATUS_DIVERGED = 2ull;   // a ghost, ADE or probe 
 constexpr uint32_t TILE_BAND = 1u;      // output region meets the 3 outer layers
 constexpr uint32_t TILE_MIXED = 2u;     // has non-fluid or out-of-grid outputs
 constexpr uint32_t TILE_SPONGE = 4u;    // meets the absorbing ramp along the outer edges
+constexpr uint32_t TILE_BAND_FLUID = 8u; // band tile whose band nodes and their 7-node windows are all fluid
 
 // Opt-in absorbing ramp along the non-periodic edges (lee_set_sponge; off by
 // default, as in the paper): damping rate (kappa / h) ((W - d) / W)^2 at a
@@ -186,6 +187,9 @@ struct BatchView {
     int n_near_strips;
     const int4 *far_tiles;      // (instance, x0, y0, 0) of the fused tiles
     int n_far_tiles;
+    // stages (bit k for stage k) whose band nodes the warp-specialised stencil
+    // does inside its band tiles; band_kernel does them in the other stages
+    int band_tile;
 };
 cudaError_t prepare_kernels(int precision);   // one-time function attributes (outside capture)
 int num_sms();
@@ -209,6 +213,7 @@ cudaError_t launch_energy(const InstDesc *dinst, const InstDesc &h, cudaStream_t
 cudaError_t launch_status_gather(const BatchView &bv, long long *out, cudaStream_t s);
 const char *stencil_kernel_name(const BatchView &bv);
 bool uses_band_pass(int precision, int kernel_mode, int tile_w, int tile_h);
+int default_band_tile_stages();         // BatchView::band_tile unless a batch sets its own
 bool tma_tile_supported(int tw, int th);
 int band_nodes(int nx, int ny, int per_x, int per_y);
 void band_chunks(int inst, int nband, std::vector<int4> &out);

@@ -477,40 +477,23 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b
 __device__ __forceinline__ float2 pair(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
 
-// One fluid node (gx, gy) of the three outer layers: one-sided DRP stencils
-// (rows 0..2 from an edge) and the radiation condition of Tam and Webb
-// dq/dt = -(cos th dq/dx + sin th dq/dy + q / (2 rho)), polar about the domain
-// centre, plus the opt-in ramp term.  Q(k-1) is read from its global planes
-// gin (p; u at +plane; v at +2 plane): the 7-node x and y windows of p, u, v
-// are loaded first, all in flight together; Q^n at (qx, qy) of qn.
+// The update of one fluid node (gx, gy) of the three outer layers from its
+// 7-node x and y windows of p, u, v (wx, wy; the node is entry tx of wx and
+// ty of wy): one-sided DRP stencils (rows 0..2 from an edge) and the radiation
+// condition of Tam and Webb dq/dt = -(cos th dq/dx + sin th dq/dy + q / (2 rho)),
+// polar about the domain centre, plus the opt-in ramp term; Q^n of the node
+// is (qp, qu, qv), the stage values come back in (op, ou, ov).  fx / fy: every
+// node of the x / y window is fluid.  Where a wall meets the band, a
+// derivative whose window holds a non-fluid node is left out of the radiation
+// condition (its one-sided row would feed back ghost values extrapolated from
+// clouds clipped by the box).  Every band path calls this, so they agree
+// bitwise.
 template <typename T>
-__device__ __forceinline__ void band_point(const T *__restrict__ gin, const QnSrc<T> &qn, int qx, int qy,
-                                           const InstDesc &d, T *out, int gx, int gy, const T *K) {
+__device__ __forceinline__ void band_update(const T (&wx)[3][7], const T (&wy)[3][7], int tx, int ty, bool fx,
+                                            bool fy, T qp, T qu, T qv, const InstDesc &d, int gx, int gy,
+                                            const T *K, T &op, T &ou, T &ov) {
     const T inv_h = K[K_INVH], half_inv_h = T(0.5) * inv_h;
     const T ad = K[K_AD], sk_h = K[K_SK];
-    const long long plane = d.plane, pitch = d.pitch;
-    int tx, ty;
-    const int sx = band_window(gx, d.nx, d.per_x, tx);
-    const int sy = band_window(gy, d.ny, d.per_y, ty);
-    T wx[3][7], wy[3][7];
-    bool fx = true, fy = true;                   // every node of the window is fluid
-#pragma unroll
-    for (int k = 0; k < 7; ++k) {
-        int xk = sx + k, yk = sy + k;
-        if (d.per_x) xk = (xk % d.nx + d.nx) % d.nx;
-        if (d.per_y) yk = (yk % d.ny + d.ny) % d.ny;
-        const long long ox = (long long)gy * pitch + xk, oy = (long long)yk * pitch + gx;
-#pragma unroll
-        for (int f = 0; f < 3; ++f) {
-            wx[f][k] = gin[f * plane + ox];
-            wy[f][k] = gin[f * plane + oy];
-        }
-        fx = fx && __ldg(d.mask + ox) == 1;
-        fy = fy && __ldg(d.mask + oy) == 1;
-    }
-    // where a wall meets the band, a derivative whose window holds a non-fluid
-    // node is left out of the radiation condition (its one-sided row would
-    // feed back ghost values extrapolated from clouds clipped by the box)
     const T dpdx = fx ? band_deriv<T>(wx[0], tx, inv_h) : T(0), dpdy = fy ? band_deriv<T>(wy[0], ty, inv_h) : T(0);
     const T dudx = fx ? band_deriv<T>(wx[1], tx, inv_h) : T(0), dudy = fy ? band_deriv<T>(wy[1], ty, inv_h) : T(0);
     const T dvdx = fx ? band_deriv<T>(wx[2], tx, inv_h) : T(0), dvdy = fy ? band_deriv<T>(wy[2], ty, inv_h) : T(0);
@@ -528,11 +511,120 @@ __device__ __forceinline__ void band_point(const T *__restrict__ gin, const QnSr
     const T rp = -(ct * dpdx + st * dpdy + p0 * q2) - sg * p0;
     const T ru = -(ct * dudx + st * dudy + u0 * q2) - sg * u0;
     const T rv = -(ct * dvdx + st * dvdy + v0 * q2) - sg * v0;
-    const long long o = (long long)gy * pitch + gx;
+    op = qp + ad * rp;
+    ou = qu + ad * ru;
+    ov = qv + ad * rv;
+}
+
+// band_update() of node (gx, gy) with Q(k-1) read from its global planes gin
+// (p; u at +plane; v at +2 plane) and Q^n at (qx, qy) of qn: the windows,
+// their mask entries and the three Q^n values are all loaded first, in flight
+// together.  Returns false (and no values) for a node that is not fluid.
+template <typename T>
+__device__ __forceinline__ bool band_values(const T *__restrict__ gin, const QnSrc<T> &qn, int qx, int qy,
+                                            const InstDesc &d, int gx, int gy, const T *K, T &op, T &ou, T &ov) {
+    const long long plane = d.plane, pitch = d.pitch;
     const long long oq = qn.at(qx, qy);
-    out[o] = qn.p[oq] + ad * rp;
-    out[plane + o] = qn.u[oq] + ad * ru;
-    out[2 * plane + o] = qn.v[oq] + ad * rv;
+    const T qp = qn.p[oq], qu = qn.u[oq], qv = qn.v[oq];
+    int tx, ty;
+    const int sx = band_window(gx, d.nx, d.per_x, tx);
+    const int sy = band_window(gy, d.ny, d.per_y, ty);
+    T wx[3][7], wy[3][7];
+    bool fx = true, fy = true;                   // every node of the window is fluid
+    bool self = false;                           // the node itself is fluid
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        int xk = sx + k, yk = sy + k;
+        if (d.per_x) xk = (xk % d.nx + d.nx) % d.nx;
+        if (d.per_y) yk = (yk % d.ny + d.ny) % d.ny;
+        const long long ox = (long long)gy * pitch + xk, oy = (long long)yk * pitch + gx;
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+            wx[f][k] = gin[f * plane + ox];
+            wy[f][k] = gin[f * plane + oy];
+        }
+        const bool mx = __ldg(d.mask + ox) == 1;
+        fx = fx && mx;
+        fy = fy && __ldg(d.mask + oy) == 1;
+        self = k == tx ? mx : self;
+    }
+    if (!self) return false;
+    band_update<T>(wx, wy, tx, ty, fx, fy, qp, qu, qv, d, gx, gy, K, op, ou, ov);
+    return true;
+}
+
+// band_values() stored at (gx, gy) of the output planes out.
+template <typename T>
+__device__ __forceinline__ void band_point(const T *__restrict__ gin, const QnSrc<T> &qn, int qx, int qy,
+                                           const InstDesc &d, T *out, int gx, int gy, const T *K) {
+    T op, ou, ov;
+    if (!band_values<T>(gin, qn, qx, qy, d, gx, gy, K, op, ou, ov)) return;
+    const long long o = (long long)gy * d.pitch + gx, plane = d.plane;
+    out[o] = op;
+    out[plane + o] = ou;
+    out[2 * plane + o] = ov;
+}
+
+// The band nodes of one tile of the warp-specialised stencil (stages 2-4),
+// done by its NC consumer threads (index c) before the tile's regular update,
+// from the tile's shared-memory box of Q(k-1) (sp, su, sv: origin at tile
+// origin - HALO, BW floats per row) and its shared copy of Q^n (qs: p, u, v
+// planes of TW x TH).  Each node's stage values replace its Q^n entries in qs
+// (only that node's own update reads them); the regular update then stores
+// them with its whole-row vector stores, so no output sector is left half
+// written.  Band nodes of the tile, in order: the rows of the top and bottom
+// layers across the tile's width, then the left and right layers' columns of
+// the other rows; node i goes to warp i % NCW, lane i / NCW (every consumer
+// warp takes its share).  TILE_BAND_FLUID tiles (the host found every band
+// node and every node of their windows fluid) read the windows from the box;
+// a node whose window leaves the box (a last tile 1 or 2 nodes wide or high)
+// and every band node of the other tiles read the global planes gin.
+template <int TW, int TH, int NC>
+__device__ __forceinline__ void band_tile(const float *sp, const float *su, const float *sv, float *qs,
+                                          const InstDesc &d, const float *gin, int x0, int y0, uint32_t flags,
+                                          const float *K, int c) {
+    constexpr int BW = TW + 2 * HALO, BH = TH + 2 * HALO, NCW = NC / 32, QP = TW * TH;
+    const int nx = d.nx, ny = d.ny;
+    const int w = min(TW, nx - x0), h = min(TH, ny - y0);
+    const int ty_lo = max(0, min(3 - y0, h)), ty_hi = max(0, min(y0 + h - (ny - 3), h));
+    const int tx_lo = max(0, min(3 - x0, w)), tx_hi = max(0, min(x0 + w - (nx - 3), w));
+    const int nrow = (ty_lo + ty_hi) * w, hm = h - ty_lo - ty_hi, cb = tx_lo + tx_hi;
+    const int nb = nrow + (hm > 0 ? hm * cb : 0);
+    const bool clean = (flags & TILE_BAND_FLUID) != 0;
+    const QnSrc<float> qn{qs, qs + QP, qs + 2 * QP, TW};
+    for (int i = (c & 31) * NCW + (c >> 5); i < nb; i += NC) {
+        int gx, gy;
+        if (i < nrow) {
+            const int r = i / w, cc = i - r * w;
+            gy = r < ty_lo ? y0 + r : y0 + h - ty_hi + (r - ty_lo);
+            gx = x0 + cc;
+        } else {
+            const int j = i - nrow, r = j / cb, cc = j - r * cb;
+            gy = y0 + ty_lo + r;
+            gx = cc < tx_lo ? x0 + cc : x0 + w - tx_hi + (cc - tx_lo);
+        }
+        int tx, ty;
+        const int bx = band_window(gx, nx, 0, tx) - x0 + HALO;     // box column of the x window
+        const int by = band_window(gy, ny, 0, ty) - y0 + HALO;     // box row of the y window
+        const int lx = gx - x0, ly = gy - y0, oq = ly * TW + lx;
+        float op, ou, ov;
+        if (!clean || bx < 0 || bx + 6 >= BW || by < 0 || by + 6 >= BH) {
+            if (!band_values<float>(gin, qn, lx, ly, d, gx, gy, K, op, ou, ov)) continue;
+        } else {
+            float wx[3][7], wy[3][7];
+            const int rx = (ly + HALO) * BW + bx, cy = by * BW + lx + HALO;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) {
+                wx[0][k] = sp[rx + k]; wx[1][k] = su[rx + k]; wx[2][k] = sv[rx + k];
+                wy[0][k] = sp[cy + k * BW]; wy[1][k] = su[cy + k * BW]; wy[2][k] = sv[cy + k * BW];
+            }
+            band_update<float>(wx, wy, tx, ty, true, true, qs[oq], qs[QP + oq], qs[2 * QP + oq], d, gx, gy, K,
+                               op, ou, ov);
+        }
+        qs[oq] = op;
+        qs[QP + oq] = ou;
+        qs[2 * QP + oq] = ov;
+    }
 }
 
 // Step 6 of Sec. 3.2 on one tile: stage update of every output node owned by
@@ -552,10 +644,12 @@ __device__ __forceinline__ void band_point(const T *__restrict__ gin, const QnSr
 // evaluated two columns per instruction; FP64: q = q^n + alpha dt RHS with
 // the DRP derivatives times 1/h.
 // QNG: Q^n is in global memory (FP32 then loads it into registers first).
-// SKIPBAND: band nodes are neither stored nor listed; band_kernel does them
-// after this kernel, reading Q^n there (stage 4 writes Q(4) over Q^n, so the
-// band nodes must keep their Q^n until then).
-template <typename T, int RY, int FL, bool QNG, bool SKIPBAND = false>
+// SKIPBAND: band nodes are not listed; band_kernel does them after this
+// kernel, reading Q^n there (stage 4 writes Q(4) over Q^n, so the band nodes
+// must keep their Q^n until then), unless BANDST: band_tile() has already put
+// their stage values in place of their Q^n entries, and they are stored from
+// there with the other nodes.
+template <typename T, int RY, int FL, bool QNG, bool SKIPBAND = false, bool BANDST = false>
 __device__ __forceinline__ void tile_points(const T *sp, const T *su, const T *sv, const int bs, const QnSrc<T> &qn,
                                             const InstDesc &d, T *out, int xt, int yt, const T *K, T src, int txi,
                                             int tyi, unsigned short *wl_idx, int *wl_n, const T *gin = nullptr) {
@@ -656,7 +750,7 @@ __device__ __forceinline__ void tile_points(const T *sp, const T *su, const T *s
                 if (MIXED && gx >= d.nx) cat[q] = 3;
                 else if (MIXED && kk[q] != 1) cat[q] = 1;
                 else if (BAND && (yband || (!d.per_x && (gx < 3 || gx > d.nx - 4)))) cat[q] = 2;
-                simple = simple && cat[q] == 0;
+                simple = simple && (cat[q] == 0 || (BANDST && cat[q] == 2));
             }
         }
         T wp[12], wu[12];
@@ -727,6 +821,11 @@ __device__ __forceinline__ void tile_points(const T *sp, const T *su, const T *s
                 o2.v[q] = n2.v[q] + ad * rv;
             }
         }
+        if (BANDST) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (cat[q] == 2) { o0.v[q] = n0.v[q]; o1.v[q] = n1.v[q]; o2.v[q] = n2.v[q]; }
+        }
         const long long o = (long long)gy * pitch + gx0;
         if (simple) {
             *reinterpret_cast<Vec4<T> *>(out + o) = o0;
@@ -735,7 +834,7 @@ __device__ __forceinline__ void tile_points(const T *sp, const T *su, const T *s
         } else {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                if (cat[q] == 0) {
+                if (cat[q] == 0 || (BANDST && cat[q] == 2)) {
                     out[o + q] = o0.v[q]; out[plane + o + q] = o1.v[q]; out[2 * plane + o + q] = o2.v[q];
                 } else if (cat[q] == 1) {
                     out[o + q] = T(0); out[plane + o + q] = T(0); out[2 * plane + o + q] = T(0);
@@ -777,8 +876,9 @@ __device__ __forceinline__ void tile_dispatch(uint32_t flags, const T *sp, const
 }
 
 // Warp-specialised kernel: band nodes are left to band_kernel, which runs
-// right after, so band tiles classify their nodes only to skip those.
-template <int RY>
+// right after, so band tiles classify their nodes only to skip those; or
+// (BANDST) band_tile() has staged their values in the tile's Q^n copy.
+template <int RY, bool BANDST>
 __device__ __forceinline__ void tile_dispatch_ws(uint32_t flags, const float *sp, const float *su, const float *sv,
                                                  const int bs, const QnSrc<float> &qn, const InstDesc &d, float *out,
                                                  int xt, int yt, const float *K, float src, int txi, int tyi) {
@@ -786,11 +886,11 @@ __device__ __forceinline__ void tile_dispatch_ws(uint32_t flags, const float *sp
     if (flags == 0)
         tile_points<float, RY, 0, false>(sp, su, sv, bs, qn, d, out, xt, yt, K, src, txi, tyi, nullptr, nullptr);
     else if (!(flags & TILE_MIXED))
-        tile_points<float, RY, B, false, true>(sp, su, sv, bs, qn, d, out, xt, yt, K, src, txi, tyi, nullptr,
-                                               nullptr);
+        tile_points<float, RY, B, false, true, BANDST>(sp, su, sv, bs, qn, d, out, xt, yt, K, src, txi, tyi,
+                                                       nullptr, nullptr);
     else
-        tile_points<float, RY, M, false, true>(sp, su, sv, bs, qn, d, out, xt, yt, K, src, txi, tyi, nullptr,
-                                               nullptr);
+        tile_points<float, RY, M, false, true, BANDST>(sp, su, sv, bs, qn, d, out, xt, yt, K, src, txi, tyi,
+                                                       nullptr, nullptr);
 }
 
 // per-warp band lists: 128 RY entries per warp, zeroed counters
@@ -1078,7 +1178,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-template <int TW, int TH, int RYT, int S_>
+template <int TW, int TH, int RYT, int S_, bool BANDT>
 __global__ void __launch_bounds__(WsGeom<TW, TH, RYT, S_>::NT, WsGeom<TW, TH, RYT, S_>::CTAS)
 stencil_ws_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ strips, int nstrips, int stage) {
     using W = WsGeom<TW, TH, RYT, S_>;
@@ -1087,6 +1187,7 @@ stencil_ws_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ st
     extern __shared__ unsigned char smem_dyn[];
     unsigned char *base = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
     __shared__ __align__(8) uint64_t full[S], empty[S];
+    __shared__ __align__(8) uint64_t bandbar;     // BANDT: every consumer warp has staged its band nodes
     __shared__ int4 info[S];           // (instance, x0, y0, flags) of the tile in each stage
     __shared__ float ssrc[S];          // source amplitude x stage forcing of that tile's instance
     __shared__ __align__(16) InstDesc sdesc[S];   // the tile's instance descriptor
@@ -1102,6 +1203,7 @@ stencil_ws_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ st
             mbar_init(&full[b], 1);
             mbar_init(&empty[b], NCW);
         }
+        mbar_init(&bandbar, NCW);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -1154,6 +1256,7 @@ stencil_ws_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ st
 
     // ---- consumers
     const int txi = tid % (TW / 4), tyi = tid / (TW / 4);
+    int nbandt = 0;                    // band tiles staged so far (BANDT): the parity of bandbar
     for (int k = 0; k < ntiles; ++k) {
         const int b = k % S;
         if (!mbar_wait_bounded(&full[b], (k / S) & 1)) {
@@ -1173,8 +1276,23 @@ stencil_ws_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ st
             const float *qs = sp + 3 * BW * BH;
             qn = QnSrc<float>{qs, qs + TW * TH, qs + 2 * TW * TH, TW};
         }
-        tile_dispatch_ws<RYT>((uint32_t)inf.w, sp, su, sv, BW, qn, d, (float *)d.q[outb], inf.y, inf.z,
-                              stage_k<float>(d, stage), ssrc[b], txi, tyi);
+        if (BANDT && (inf.w & TILE_BAND)) {
+            // stages 2-4: the band nodes' stage values go into the tile's Q^n
+            // copy first; every consumer warp waits until all are in place
+            float *qs = reinterpret_cast<float *>(base + (size_t)b * W::STAGE_BYTES) + 3 * BW * BH;
+            band_tile<TW, TH, W::NC>(sp, su, sv, qs, d, (const float *)d.q[inb], inf.y, inf.z, (uint32_t)inf.w,
+                                     stage_k<float>(d, stage), tid);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bandbar);
+            if (!mbar_wait_bounded(&bandbar, nbandt & 1)) {
+                abort_flag = 1;
+                if (lane == 0) flag_block_timeout(inst, strips, nstrips);
+            }
+            ++nbandt;
+            if (abort_flag) break;
+        }
+        tile_dispatch_ws<RYT, BANDT>((uint32_t)inf.w, sp, su, sv, BW, qn, d, (float *)d.q[outb], inf.y, inf.z,
+                                     stage_k<float>(d, stage), ssrc[b], txi, tyi);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[b]);
     }
@@ -1281,6 +1399,10 @@ int pair_tile_h() { return PAIR_TH; }
 // Band node b of a non-periodic instance: rows 0..2 and ny-3..ny-1 over the
 // full width (6 nx nodes), then columns 0..2 and nx-3..nx-1 of rows 3..ny-4.
 constexpr int BAND_CHUNK = 128;             // band nodes per band_kernel block iteration
+// stages whose band nodes the stencil does inside its band tiles by default:
+// none (on the 512-instance sweep the in-tile band made the stage-2 launch
+// 1.77 ms against 1.43 + 0.20 ms for the stencil and the band pass)
+constexpr int BAND_TILE_STAGES = 0;
 int band_nodes(int nx, int ny, int per_x, int per_y) {
     return (per_x || per_y || nx < 6 || ny < 6) ? 0 : 6 * nx + 6 * (ny - 6);
 }
@@ -1314,7 +1436,6 @@ band_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ chunks, 
             const int r = b / 6, c = b - 6 * r;
             gy = 3 + r; gx = c < 3 ? c : nx - 6 + c;
         }
-        if (__ldg(d.mask + (long long)gy * d.pitch + gx) != 1) continue;
         const T *P = (const T *)d.q[inb];
         const T *Q0 = (const T *)d.q[0];
         const long long plane = d.plane;
@@ -1477,17 +1598,35 @@ template <int TW, int TH, int RYT> cudaError_t tma_attr() {
 }
 
 template <int TW, int TH, int RYT, int S_> cudaError_t ws_attr() {
-    return cudaFuncSetAttribute(stencil_ws_kernel<TW, TH, RYT, S_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(stencil_ws_kernel<TW, TH, RYT, S_, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WsGeom<TW, TH, RYT, S_>::SMEM);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(stencil_ws_kernel<TW, TH, RYT, S_, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)WsGeom<TW, TH, RYT, S_>::SMEM);
+}
+
+// stages whose band nodes the warp-specialised stencil does inside its band
+// tiles (bit k for stage k) unless a batch chooses; the others leave them to
+// band_kernel.  LEE_BAND_TILE overrides (a bit mask, e.g. 0 or 30).
+int default_band_tile_stages() {
+    static const int m = [] {
+        const char *e = getenv("LEE_BAND_TILE");
+        return e ? (atoi(e) & 28) : BAND_TILE_STAGES;
+    }();
+    return m;
 }
 
 template <int TW, int TH, int RYT, int S_>
 void launch_ws(const BatchView &bv, int stage, int persistent_ctas, cudaStream_t s) {
     using W = WsGeom<TW, TH, RYT, S_>;
     const int grid = std::min(bv.nstrips, persistent_ctas > 0 ? persistent_ctas : W::CTAS * num_sms());
-    if (grid > 0)           // no tiles left (every tile fused): only the band pass
-        stencil_ws_kernel<TW, TH, RYT, S_><<<grid, W::NT, W::SMEM, s>>>(bv.inst, bv.strips, bv.nstrips, stage);
-    if (bv.nband_chunks > 0) {
+    const int in_tile = grid > 0 && stage >= 2 && ((bv.band_tile >> stage) & 1);
+    // grid == 0: no tiles left (every tile fused), only the band pass
+    if (grid > 0 && in_tile)
+        stencil_ws_kernel<TW, TH, RYT, S_, true><<<grid, W::NT, W::SMEM, s>>>(bv.inst, bv.strips, bv.nstrips, stage);
+    else if (grid > 0)
+        stencil_ws_kernel<TW, TH, RYT, S_, false><<<grid, W::NT, W::SMEM, s>>>(bv.inst, bv.strips, bv.nstrips, stage);
+    if (bv.nband_chunks > 0 && !in_tile) {
         static const int per_sm = [] {
             int n = 0;
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, band_kernel<float>, BAND_CHUNK, 0) != cudaSuccess || n < 1)

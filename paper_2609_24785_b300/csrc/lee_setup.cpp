@@ -484,6 +484,19 @@ int build_plan(int nx, int ny, double h, double x0, double y0, int per_x, int pe
             for (int j = ya; j < std::min(yb, ny) && !(f & TILE_MIXED); ++j)
                 for (int i = xa; i < std::min(xb, nx); ++i)
                     if (P.kind[(size_t)j * nx + i] != 1) { f |= TILE_MIXED; break; }
+            if ((f & TILE_BAND) && !per_x && !per_y && nx >= 7 && ny >= 7) {
+                // every band node of the tile, and every node of its x and y
+                // windows (7 nodes, one-sided near an edge), is fluid
+                bool fluid = true;
+                auto ok = [&](int i, int j) { return P.kind[(size_t)j * nx + i] == 1; };
+                for (int j = ya; j < std::min(yb, ny) && fluid; ++j)
+                    for (int i = xa; i < std::min(xb, nx) && fluid; ++i) {
+                        if (!(j < 3 || j > ny - 4 || i < 3 || i > nx - 4)) continue;
+                        const int sx = std::min(std::max(i - 3, 0), nx - 7), sy = std::min(std::max(j - 3, 0), ny - 7);
+                        for (int k = 0; k < 7 && fluid; ++k) fluid = ok(sx + k, j) && ok(i, sy + k);
+                    }
+                if (fluid) f |= TILE_BAND_FLUID;
+            }
             P.tile_flags[(size_t)ty * P.tiles_x + tx] = f;
         }
     return LEE_OK;

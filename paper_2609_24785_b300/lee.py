@@ -65,6 +65,8 @@ SIGNATURES = {
     "lee_set_impedance_rational": (C.c_int, [_vp, C.c_int, _dp, C.c_int, _dp]),
     "lee_batch_set_stage_fusion": (C.c_int, [_vp, C.c_int]),
     "lee_batch_fused_tiles": (C.c_int, [_vp, _llp, _llp]),
+    "lee_batch_set_band_in_tile": (C.c_int, [_vp, C.c_int]),
+    "lee_batch_band_in_tile": (C.c_int, [_vp, C.POINTER(C.c_int)]),
     "lee_fp64_fma_probe": (C.c_int, [C.c_int, C.c_longlong, _vp, _vp]),
     "lee_plan": (C.c_int, [_vp, C.POINTER(lee_sizes)]),
     "lee_bind": (C.c_int, [_vp, _vp, C.c_longlong, _vp]),
@@ -379,6 +381,18 @@ class Batch:
         and ramp (FP32, 64 x 40 tiles); results bitwise those of the unfused
         stages."""
         self._c(self.L.lee_batch_set_stage_fusion(self.b, int(bool(on))))
+
+    def set_band_in_tile(self, stage_mask=-1):
+        """Stages (bit k for stage k) whose band nodes the warp-specialised
+        stencil updates inside its band tiles instead of a separate band pass
+        (-1: the default); both give bitwise the same values."""
+        self._c(self.L.lee_batch_set_band_in_tile(self.b, int(stage_mask)))
+
+    def band_in_tile(self):
+        """The stage mask in effect (see set_band_in_tile)."""
+        m = C.c_int()
+        self._c(self.L.lee_batch_band_in_tile(self.b, C.byref(m)))
+        return m.value
 
     def fused_tiles(self):
         """(tiles the fused pass covers, all tiles)."""

@@ -163,16 +163,47 @@ def _edge_cases():
                         probes=np.array([[2.0 * h, 30.0 * h]]), steps=200)
     c3 = workloads.Case("edge_203x9", 203, 9, init=("pulse", 198.0 * h, 4.0 * h, 1.0, 2 * h),
                         probes=np.array([[201.0 * h, 2.0 * h]]), steps=60)
-    return [c1, c2, c3]
+    # last tile column 2 wide and last tile row 2 high (64 x 40 tiles): band
+    # windows that leave the tile's box
+    c4 = workloads.Case("edge_130x122", 130, 122, init=("pulse", 124.0 * h, 116.0 * h, 1.0, 2 * h),
+                        probes=np.array([[128.0 * h, 120.0 * h]]), steps=80)
+    return [c1, c2, c3, c4]
 
 
 @pytest.mark.parametrize("case", _edge_cases(), ids=lambda c: c.name)
 def test_band_pass_ragged_edges_fp32(case, cuda_device):
-    """FP32 bulk: the outer three layers are done by the band pass after the
-    warp-specialised stencil; ragged tiles along both axes, masked edge nodes
-    and waves crossing the one-sided stencils and the radiation condition,
-    against the oracle."""
+    """FP32 bulk: the outer three layers are done inside the warp-specialised
+    stencil's band tiles (or by the band pass after it); ragged tiles along
+    both axes, masked edge nodes and waves crossing the one-sided stencils and
+    the radiation condition, against the oracle."""
     _check(case, "fp32")
+
+
+def test_band_in_tile_equals_band_pass(cuda_device):
+    """The band nodes updated inside the stencil's band tiles from the tile's
+    shared-memory box (lee_batch_set_band_in_tile) equal bitwise those of the
+    separate band pass over the global planes, in every stage, for a batch
+    with walls clear of the band (a sweep cylinder), a wall crossing both side
+    columns (tiles whose band windows hold non-fluid nodes), ragged last tiles
+    1 and 2 nodes wide or high (windows that leave the box), and the ramp."""
+    cases, _ = workloads.sweep(1, seed=11, sizes=(512,))
+    cases += _edge_cases()
+    runs = []
+    for mask in (0, 28, 20):
+        batch = lee.Batch("fp32")
+        members = [make_solver(c, "fp32") for c in cases]
+        for m in members:
+            batch.add(m)
+        batch.set_band_in_tile(mask)
+        assert batch.band_in_tile() == mask
+        batch.step(30)
+        batch.sync()
+        assert not batch.status().any()
+        runs.append([[m.field(f) for f in range(3)] + [m.ade()] for m in members])
+    for other in runs[1:]:
+        for a, b in zip(runs[0], other):
+            for x, y in zip(a, b):
+                assert np.array_equal(x, y)
 
 
 def test_small_grids_fp32(cuda_device):
