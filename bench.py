@@ -155,6 +155,20 @@ def dist_setup(args):
     return ws, rank, local
 
 
+def aggregate_over_ranks(ms, fluid, device):
+    """Replicas (one process per GPU, independent instances, no collective on
+    the data path): the job's time is the slowest rank's, its work the sum of
+    every rank's fluid nodes.  device: where the process group's tensors live
+    (the rank's GPU for NCCL, the CPU for gloo)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    f = torch.tensor([float(fluid)], dtype=torch.float64, device=device)
+    dist.all_reduce(f)
+    return float(t.item()), float(f.item())
+
+
 def cpu_baseline(case, target_seconds=15.0):
     """The FP64 oracle as it stands, on one instance of the workload, on all host
     cores (OpenMP); runs a bounded number of steps."""
@@ -364,13 +378,7 @@ def run_lee(args):
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        f = torch.tensor([float(fluid)], device=dev)
-        dist.all_reduce(f)
-        fluid_all = float(f.item())
+        ms, fluid_all = aggregate_over_ranks(ms, fluid, dev)
     else:
         fluid_all = float(fluid)
     value = fluid_all * 4 * args.steps / (ms / 1e3) / 1e6
