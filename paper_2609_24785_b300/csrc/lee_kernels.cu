@@ -1416,31 +1416,38 @@ void band_chunks(int inst, int nband, std::vector<int4> &out) {
 // After the warp-specialised stencil of a stage: every fluid node of the three
 // outer layers is redone by one thread (band_point on the global planes).  A
 // block takes whole chunks of one instance, so the instance is known before
-// any per-node load.
+// any per-node load; the next chunk's entry is loaded one chunk ahead.  Six
+// blocks per SM (80 registers): 7 % faster on the sweep than five at 92 and
+// than eight at 64 (spills).
 template <typename T>
-__global__ void __launch_bounds__(BAND_CHUNK)
+__global__ void __launch_bounds__(BAND_CHUNK, 6)
 band_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ chunks, int nchunks, int stage) {
     const int inb = stage_in(stage), outb = stage_out(stage);
-    for (int ci = blockIdx.x; ci < nchunks; ci += gridDim.x) {
-        const int4 ch = __ldg(chunks + ci);
-        if ((int)threadIdx.x >= ch.z) continue;
-        const InstDesc &d = inst[ch.x];
-        const int nx = d.nx, ny = d.ny;
-        int b = ch.y + threadIdx.x, gx, gy;
-        if (b < 3 * nx) {
-            gy = b / nx; gx = b - gy * nx;
-        } else if (b < 6 * nx) {
-            b -= 3 * nx; gy = ny - 3 + b / nx; gx = b % nx;
-        } else {
-            b -= 6 * nx;
-            const int r = b / 6, c = b - 6 * r;
-            gy = 3 + r; gx = c < 3 ? c : nx - 6 + c;
+    int ci = blockIdx.x;
+    int4 ch = ci < nchunks ? __ldg(chunks + ci) : make_int4(0, 0, 0, 0);
+    for (; ci < nchunks; ci += gridDim.x) {
+        const int cn = ci + gridDim.x;
+        const int4 next = cn < nchunks ? __ldg(chunks + cn) : ch;
+        if ((int)threadIdx.x < ch.z) {
+            const InstDesc &d = inst[ch.x];
+            const int nx = d.nx, ny = d.ny;
+            int b = ch.y + threadIdx.x, gx, gy;
+            if (b < 3 * nx) {
+                gy = b / nx; gx = b - gy * nx;
+            } else if (b < 6 * nx) {
+                b -= 3 * nx; gy = ny - 3 + b / nx; gx = b % nx;
+            } else {
+                b -= 6 * nx;
+                const int r = b / 6, c = b - 6 * r;
+                gy = 3 + r; gx = c < 3 ? c : nx - 6 + c;
+            }
+            const T *P = (const T *)d.q[inb];
+            const T *Q0 = (const T *)d.q[0];
+            const long long plane = d.plane;
+            const QnSrc<T> qn{Q0, Q0 + plane, Q0 + 2 * plane, d.pitch};
+            band_point<T>(P, qn, gx, gy, d, (T *)d.q[outb], gx, gy, stage_k<T>(d, stage));
         }
-        const T *P = (const T *)d.q[inb];
-        const T *Q0 = (const T *)d.q[0];
-        const long long plane = d.plane;
-        const QnSrc<T> qn{Q0, Q0 + plane, Q0 + 2 * plane, d.pitch};
-        band_point<T>(P, qn, gx, gy, d, (T *)d.q[outb], gx, gy, stage_k<T>(d, stage));
+        ch = next;
     }
 }
 

@@ -206,6 +206,29 @@ def test_band_in_tile_equals_band_pass(cuda_device):
                 assert np.array_equal(x, y)
 
 
+def test_degenerate_inputs(cuda_device):
+    """Zero steps leave the state alone; a batch whose members have all left
+    steps with no work and reports no status; a wall line that misses the box
+    (no ghost point, no solid node) gives the free-field result."""
+    case = workloads.cylinder_pulse(256, steps=10)
+    s = make_solver(case, "fp32")
+    before = [s.field(f) for f in range(3)]
+    s.step(0)
+    assert all(np.array_equal(a, s.field(f)) for f, a in enumerate(before))
+    batch = lee.Batch("fp32")
+    batch.add(s)
+    batch.remove(s)
+    batch.step(5)
+    batch.sync()
+    assert batch.status().size == 0
+    assert all(np.array_equal(a, s.field(f)) for f, a in enumerate(before))
+    h = workloads.H
+    far = workloads.Case("wall_outside_box", 96, 80, wall=("line", 0.5, -1.0, 0.0), imp=("msd", 1.0, 0.05, 5.0),
+                         init=("pulse", 48 * h, 40 * h, 1.0, 3 * h), probes=np.array([[10 * h, 12 * h]]), steps=60)
+    assert make_solver(far, "fp32", bind=False).sizes.n_ghost == 0
+    _check(far, "fp32")
+
+
 def test_small_grids_fp32(cuda_device):
     """The band pass on grids with few interior rows (40 x 24: 18 rows between
     the top and bottom layers; 8 x 8: 2)."""
