@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lee", choices=["lee", "reference"])
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "cylinder", "free", "flat", "monopole"])
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "rational", "cylinder", "free", "flat", "monopole"])
     ap.add_argument("--count", type=int, default=512)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
@@ -86,6 +86,12 @@ def workload_cases(args, rank, accept=None):
         cases, rejected = workloads.sweep(args.count, seed=24785 + rank, accept=accept)
         desc = ("batched cylinder-pulse sweep: %d instances, n^2 with n in {256,384,512,768,1024}, "
                 "cylinder r = 0.1 n, R/M/K log-uniform, seed %d" % (args.count, 24785 + rank))
+        return cases, rejected, desc
+    if args.workload == "rational":
+        cases, rejected = workloads.rational_sweep(args.count, seed=24785 + rank, accept=accept)
+        desc = ("batched cylinder-pulse sweep with broadband walls: %d instances, n^2 with n in "
+                "{256,384,512,768,1024}, cylinder r = 0.1 n, two real poles + one complex pair "
+                "(4 ADE states per ghost), seed %d" % (args.count, 24785 + rank))
         return cases, rejected, desc
     if args.workload == "free":
         # diagnostic: no wall, so every tile away from the outer band is interior

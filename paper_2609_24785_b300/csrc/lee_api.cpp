@@ -761,10 +761,8 @@ int lee_write_state(lee_ctx *ctx, const void *blob) {
     CK(cudaMemsetAsync(ctx->hd.clock + 2, 0, sizeof(long long), ctx->stream));   // status: healthy
     CK(cudaMemcpyAsync(ctx->hd.q[0], b + 16, qb, cudaMemcpyHostToDevice, ctx->stream));
     const size_t xb = 8 * (size_t)ctx->hd.ns * ctx->hd.ng;
-    if (ctx->hd.ng) {
-        CK(cudaMemcpyAsync(ctx->hd.Xn, b + 16 + qb, xb, cudaMemcpyHostToDevice, ctx->stream));
-        CK(cudaMemcpyAsync(ctx->hd.Xs, b + 16 + qb, xb, cudaMemcpyHostToDevice, ctx->stream));
-    }
+    // X^n only: stage 1 reads the step's starting ADE state from X^n
+    if (ctx->hd.ng) CK(cudaMemcpyAsync(ctx->hd.Xn, b + 16 + qb, xb, cudaMemcpyHostToDevice, ctx->stream));
     if (ctx->hd.np) CK(cudaMemcpyAsync(ctx->hd.p_hist, b + 16 + qb + xb,
                                        8 * (size_t)ctx->hd.np * ctx->hd.pcap, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -781,10 +779,8 @@ int lee_upload_state_async(lee_ctx *ctx, const void *blob) {
     CK(cudaMemsetAsync(ctx->hd.clock + 2, 0, sizeof(long long), ctx->stream));   // status: healthy
     CK(cudaMemcpyAsync(ctx->hd.q[0], b + 16, qb, cudaMemcpyHostToDevice, ctx->stream));
     const size_t xb = 8 * (size_t)ctx->hd.ns * ctx->hd.ng;
-    if (ctx->hd.ng) {
-        CK(cudaMemcpyAsync(ctx->hd.Xn, b + 16 + qb, xb, cudaMemcpyHostToDevice, ctx->stream));
-        CK(cudaMemcpyAsync(ctx->hd.Xs, b + 16 + qb, xb, cudaMemcpyHostToDevice, ctx->stream));
-    }
+    // X^n only: stage 1 reads the step's starting ADE state from X^n
+    if (ctx->hd.ng) CK(cudaMemcpyAsync(ctx->hd.Xn, b + 16 + qb, xb, cudaMemcpyHostToDevice, ctx->stream));
     return LEE_OK;
 }
 

@@ -157,6 +157,10 @@ ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int4 *__restric
     const InstDesc &d = inst[ch.x];
     const int g = ch.y + sub;
     const int e0 = __ldg(d.g_start + g), e1 = __ldg(d.g_start + g + 1);
+    // the ADE state of the stage: at stage 1 the step's starting state X^n,
+    // which stage 4 of the previous step left in both buffers (so a state
+    // upload writes X^n only)
+    const double *Xc = stage == 1 ? d.Xn : d.Xs;
     // per-ghost data, fetched before the gather so that the latencies overlap:
     // into registers (FP64 gathers), or by cp.async into shared memory
     // (float-float gather, whose registers go to more resident warps)
@@ -169,7 +173,7 @@ ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int4 *__restric
     if (lane == 0) {
         if constexpr (GA == GA_FF) {
             if constexpr (!GEN) {
-                cp_async16(&s_x[sub], d.Xs + 2 * g);        // 16-byte aligned: 2 doubles per ghost
+                cp_async16(&s_x[sub], Xc + 2 * g);          // 16-byte aligned: 2 doubles per ghost
                 cp_async16(&s_xn[sub], d.Xn + 2 * g);
             }
             cp_async16(&s_n[sub], d.g_n + g);
@@ -177,7 +181,7 @@ ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int4 *__restric
             cp_async4(&s_t[sub], d.g_target + g);
         } else {
             if constexpr (!GEN) {
-                x0 = d.Xs[2 * g]; x1 = d.Xs[2 * g + 1];
+                x0 = Xc[2 * g]; x1 = Xc[2 * g + 1];
                 xn0 = d.Xn[2 * g]; xn1 = d.Xn[2 * g + 1];
             }
             n = __ldg(d.g_n + g);
@@ -300,7 +304,7 @@ ghost_kernel(const InstDesc *__restrict__ inst, int ninst, const int4 *__restric
         const double *Am = d.ade, *bv = Am + ns * ns, *cv = bv + ns;
         double xv[MAX_ADE_STATES], xd[MAX_ADE_STATES];
 #pragma unroll
-        for (int i = 0; i < MAX_ADE_STATES; ++i) xv[i] = i < ns ? d.Xs[(long long)ns * g + i] : 0.0;
+        for (int i = 0; i < MAX_ADE_STATES; ++i) xv[i] = i < ns ? Xc[(long long)ns * g + i] : 0.0;
         double un = 0.0, dun = 0.0;
 #pragma unroll
         for (int i = 0; i < MAX_ADE_STATES; ++i) {

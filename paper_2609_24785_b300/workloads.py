@@ -135,6 +135,33 @@ def sweep(count=512, seed=24785, steps=2000, accept: Optional[Callable[[Case], b
     return out, rejected
 
 
+def rational_sweep(count=512, seed=24785, steps=2000, accept: Optional[Callable[[Case], bool]] = None,
+                   sizes=SWEEP_SIZES, sponge=LONG_RUN_SPONGE) -> Tuple[List[Case], int]:
+    """The sweep's geometry with broadband walls (Sec. 2.3, Eq. Yrational with
+    Y_inf = 0): two real poles lam in -[5, 200] with residues A in [0.5, 10],
+    and one complex pair alpha +- i beta, alpha in -[5, 50], beta in [10, 60],
+    residue B + i C with B in [1, 20] and C = -B alpha / beta (so that the pair's
+    numerator is a pure multiple of s, as for a mass-spring-damper); all
+    log-uniform: four ADE states per ghost point."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    lu = lambda a, b: float(np.exp(rng.uniform(np.log(a), np.log(b))))
+    out, rejected = [], 0
+    while len(out) < count:
+        n = int(rng.choice(sizes))
+        real = [(-lu(5.0, 200.0), lu(0.5, 10.0)) for _ in range(2)]
+        al, be, B = -lu(5.0, 50.0), lu(10.0, 60.0), lu(1.0, 20.0)
+        pairs = [(al, be, B, -B * al / be)]
+        c = ((n - 1) / 2 * H, (n - 1) / 2 * H)
+        case = Case("rational_sweep_%d_n%d" % (len(out), n), n, n, wall=("cyl", c[0], c[1], 0.1 * n * H),
+                    imp=("rational", real, pairs), init=("pulse", c[0] + 0.25 * n * H, c[1], 1.0, 4 * H),
+                    probes=np.array([[c[0] + 0.15 * n * H, c[1]]]), steps=steps, sponge=sponge)
+        if accept is None or accept(case):
+            out.append(case)
+        else:
+            rejected += 1
+    return out, rejected
+
+
 SERVE_SIZES = (256, 384, 512, 768, 1024, 1536, 2048)
 
 
