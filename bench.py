@@ -459,10 +459,12 @@ def run_lee(args):
     if not args.no_e2e:
         import ctypes as C
         blobs = [torch.from_numpy(s.read_state()).pin_memory() for s in solvers]
-        pr = [torch.empty(max(s._nprobe, 1), dtype=torch.float64).pin_memory() for s in solvers]
-        recs = [int(np.frombuffer(b.numpy()[:16].tobytes(), dtype=np.int64)[1]) for b in blobs]
+        # every member's probe record of the step, gathered on the device and
+        # read back in one copy
+        npv = batch.latest_probe_count()
+        pr = torch.empty(max(npv, 1), dtype=torch.float64).pin_memory()
         h2d = sum(b.numel() for b in blobs)
-        d2h = sum(8 * s._nprobe for s in solvers)
+        d2h = 8 * npv
         L = lee.load()
         torch.cuda.synchronize()
         barrier()
@@ -471,10 +473,7 @@ def run_lee(args):
             for s, b in zip(solvers, blobs):
                 lee._check(L.lee_upload_state_async(s.ctx, C.c_void_p(b.data_ptr())), s.ctx)
             batch.step(1)
-            for s, p, r in zip(solvers, pr, recs):
-                if s._nprobe and r < 4096:
-                    rec = r   # the uploaded state carries the record count; this step writes record r
-                    lee._check(L.lee_download_probes_async(s.ctx, C.cast(C.c_void_p(p.data_ptr()), lee._dp), rec, 1), s.ctx)
+            batch.read_latest_probes_async(pr.data_ptr())
             stream.synchronize()
         el = time.perf_counter() - t0
         barrier()

@@ -295,6 +295,13 @@ int lee_batch_band_in_tile(lee_batch *b, int *stage_mask);
 /* Tiles that the fused pass covers and the batch's total tiles (after the
  * members are final; refreshes the batch's tables). */
 int lee_batch_fused_tiles(lee_batch *b, long long *fused, long long *total);
+/* The latest probe record of every member with probes (record steps-1 of
+ * each, Sec. 4 microphones; NaN before the first), members in batch order,
+ * each member's probes in its lee_set_probes order, written to host (count
+ * doubles; pinned memory keeps the copy asynchronous) by one gather kernel and
+ * one copy on the batch stream: it is complete after the stream drains.
+ * host = NULL returns the count only. */
+int lee_batch_read_latest_probes_async(lee_batch *b, double *host, long long *count);
 /* Name of the stencil kernel variant the batch launches (static string; ""
  * before lee_batch_bind or without members). */
 const char *lee_batch_stencil_kernel(lee_batch *b);

@@ -98,6 +98,9 @@ struct lee_batch {
     bool dirty = true;
     BatchView bv{};
     long long *status = nullptr;      // device: members' status words (lee_batch_status)
+    int *probe_off = nullptr;         // device: offsets of the members' latest probe records
+    double *probe_buf = nullptr;      // device: the latest probe records, side by side
+    long long nprobe_values = 0;      // their total count
     int strips_per_sm = 2;            // lee_batch_set_strips_per_sm
     int fuse12 = 0;                   // lee_batch_set_stage_fusion
     int band_tile = -1;               // lee_batch_set_band_in_tile (-1: default_band_tile_stages())
@@ -883,8 +886,11 @@ static long long batch_bytes(const lee_batch *b) {
         nst += (size_t)c->hd.tiles_x * c->hd.tiles_y;
         nbc += c->nbchunks;
     }
+    size_t npv = 1;
+    for (auto *c : b->members) npv += c->hd.np;
     return (long long)(align_up(n * sizeof(InstDesc)) + 2 * align_up((n + 1) * 4) + align_up(nch * sizeof(int4)) +
-                       3 * align_up(nst * sizeof(int4)) + align_up(n * sizeof(long long)) + align_up(nbc * sizeof(int4)));
+                       3 * align_up(nst * sizeof(int4)) + align_up(n * sizeof(long long)) + align_up(nbc * sizeof(int4)) +
+                       align_up((n + 1) * 4) + align_up(npv * 8));
 }
 
 int lee_batch_plan(lee_batch *b, long long *device_bytes) {
@@ -971,6 +977,14 @@ static int batch_refresh(lee_batch *b) {
                  o_status = o_far + align_up(far.size() * sizeof(int4)),
                  o_bc = o_status + align_up(n * sizeof(long long));
     b->status = (long long *)(b->dev + o_status);
+    // the members' latest probe records side by side (lee_batch_read_latest_probes_async)
+    std::vector<int> poff(pi.size() + 1, 0);
+    for (size_t i = 0; i < pi.size(); ++i) poff[i + 1] = poff[i] + (n ? descs[pi[i]].np : 0);
+    const size_t o_poff = o_bc + align_up(std::max<size_t>(bch.size(), 1) * sizeof(int4)),
+                 o_pbuf = o_poff + align_up((n + 1) * 4);
+    b->probe_off = (int *)(b->dev + o_poff);
+    b->probe_buf = (double *)(b->dev + o_pbuf);
+    b->nprobe_values = poff.back();
     cudaError_t e;
     if (n) {
         if ((e = cudaMemcpyAsync(b->dev + o_desc, descs.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice, b->stream)) ||
@@ -982,6 +996,7 @@ static int batch_refresh(lee_batch *b) {
             (e = cudaMemcpyAsync(b->dev + o_far, far.data(), far.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream)) ||
             (bch.size() && (e = cudaMemcpyAsync(b->dev + o_bc, bch.data(), bch.size() * sizeof(int4),
                                                 cudaMemcpyHostToDevice, b->stream))) ||
+            (e = cudaMemcpyAsync(b->dev + o_poff, poff.data(), poff.size() * 4, cudaMemcpyHostToDevice, b->stream)) ||
             (e = cudaStreamSynchronize(b->stream))) {
             b->err = std::string("batch upload: ") + cudaGetErrorString(e);
             return LEE_ERR_CUDA;
@@ -1080,6 +1095,24 @@ int lee_batch_fused_tiles(lee_batch *b, long long *fused, long long *total) {
     }
     *fused = b->bv.fuse12 ? b->bv.n_far_tiles : 0;
     *total = b->bv.total_tiles;
+    return LEE_OK;
+}
+
+int lee_batch_read_latest_probes_async(lee_batch *b, double *host, long long *count) {
+    if (!b || !count) return LEE_ERR_ARG;
+    if (!b->dev) { b->err = "batch not bound"; return LEE_ERR_ARG; }
+    if (b->dirty) {
+        const int rc = batch_refresh(b);
+        if (rc != LEE_OK) return rc;
+    }
+    *count = b->nprobe_values;
+    if (!host || b->nprobe_values == 0) return LEE_OK;
+    cudaError_t e;
+    if ((e = launch_probe_latest(b->bv, b->probe_off, b->probe_buf, b->stream)) ||
+        (e = cudaMemcpyAsync(host, b->probe_buf, (size_t)b->nprobe_values * 8, cudaMemcpyDeviceToHost, b->stream))) {
+        b->err = std::string("batch probes: ") + cudaGetErrorString(e);
+        return LEE_ERR_CUDA;
+    }
     return LEE_OK;
 }
 

@@ -203,6 +203,9 @@ cudaError_t launch_ghost(const BatchView &bv, int stage, cudaStream_t s);
 bool ghost_float_float(int precision);
 cudaError_t launch_stencil(const BatchView &bv, int stage, int persistent_ctas, cudaStream_t s);
 cudaError_t launch_probes(const BatchView &bv, cudaStream_t s);
+// the latest probe record of every instance with probes into dst (instance
+// bv.probe_inst[i] at dst + off[i], device arrays)
+cudaError_t launch_probe_latest(const BatchView &bv, const int *off, double *dst, cudaStream_t s);
 cudaError_t launch_pair(const BatchView &bv, cudaStream_t s);   // fused stages 1 + 2 on bv.far_tiles
 int pair_tile_w();
 int pair_tile_h();

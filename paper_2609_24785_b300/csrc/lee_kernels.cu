@@ -1472,6 +1472,25 @@ __global__ void probe_kernel(const InstDesc *__restrict__ inst, const int *__res
     if (threadIdx.x == 0) d.clock[1] = rec + 1;
 }
 
+// The latest probe record (record clock[1] - 1) of every instance with probes,
+// side by side: instance probe_inst[i]'s values at dst + off[i]; NaN before a
+// first record or past the capacity.
+__global__ void probe_latest_kernel(const InstDesc *__restrict__ inst, const int *__restrict__ probe_inst,
+                                    const int *__restrict__ off, double *__restrict__ dst) {
+    const InstDesc &d = inst[probe_inst[blockIdx.x]];
+    const long long rec = d.clock[1] - 1;
+    double *o = dst + off[blockIdx.x];
+    for (int p = threadIdx.x; p < d.np; p += blockDim.x)
+        o[p] = rec >= 0 && rec < d.pcap ? d.p_hist[rec * d.np + p] : __longlong_as_double(0x7ff8000000000000LL);
+}
+
+cudaError_t launch_probe_latest(const BatchView &bv, const int *off, double *dst, cudaStream_t s) {
+    if (bv.nprobe_inst == 0) return cudaSuccess;
+    probe_latest_kernel<<<bv.nprobe_inst, 128, 0, s>>>(bv.inst, bv.probe_inst, off, dst);
+    count_launch();
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- init / staging / energy
 template <typename T>
 __global__ void init_kernel(const InstDesc *__restrict__ dd, int kind, double a0, double a1, double a2,

@@ -66,6 +66,7 @@ SIGNATURES = {
     "lee_batch_set_stage_fusion": (C.c_int, [_vp, C.c_int]),
     "lee_batch_fused_tiles": (C.c_int, [_vp, _llp, _llp]),
     "lee_batch_set_band_in_tile": (C.c_int, [_vp, C.c_int]),
+    "lee_batch_read_latest_probes_async": (C.c_int, [_vp, _dp, _llp]),
     "lee_batch_band_in_tile": (C.c_int, [_vp, C.POINTER(C.c_int)]),
     "lee_fp64_fma_probe": (C.c_int, [C.c_int, C.c_longlong, _vp, _vp]),
     "lee_plan": (C.c_int, [_vp, C.POINTER(lee_sizes)]),
@@ -381,6 +382,27 @@ class Batch:
         and ramp (FP32, 64 x 40 tiles); results bitwise those of the unfused
         stages."""
         self._c(self.L.lee_batch_set_stage_fusion(self.b, int(bool(on))))
+
+    def latest_probe_count(self):
+        """Values that read_latest_probes returns (every member's probe count)."""
+        n = C.c_longlong()
+        self._c(self.L.lee_batch_read_latest_probes_async(self.b, C.cast(None, _dp), C.byref(n)))
+        return n.value
+
+    def read_latest_probes_async(self, host_ptr):
+        """Enqueue the gather of every member's latest probe record into host
+        memory at host_ptr (latest_probe_count() doubles, pinned for an
+        asynchronous copy) on the batch stream."""
+        n = C.c_longlong()
+        self._c(self.L.lee_batch_read_latest_probes_async(self.b, C.cast(C.c_void_p(host_ptr), _dp), C.byref(n)))
+        return n.value
+
+    def read_latest_probes(self):
+        """Every member's latest probe record, members in order (synchronous)."""
+        out = np.zeros(max(self.latest_probe_count(), 1))
+        self.read_latest_probes_async(out.ctypes.data)
+        self.sync()
+        return out[:self.latest_probe_count()]
 
     def set_band_in_tile(self, stage_mask=-1):
         """Stages (bit k for stage k) whose band nodes the warp-specialised

@@ -229,6 +229,25 @@ def test_degenerate_inputs(cuda_device):
     _check(far, "fp32")
 
 
+def test_batch_latest_probes_gather(cuda_device):
+    """lee_batch_read_latest_probes_async: every member's latest probe record,
+    members in order, equal to the last row of each member's own history
+    (members with different probe counts, one without probes)."""
+    cases, _ = workloads.sweep(2, seed=5, sizes=(256,))
+    flat = workloads.flat_wall(128, steps=20)
+    bare = workloads.cylinder_pulse(256, steps=20)
+    bare.probes = np.zeros((0, 2))
+    members = [make_solver(c, "fp32", probe_capacity=64) for c in cases + [flat, bare]]
+    batch = lee.Batch("fp32")
+    for m in members:
+        batch.add(m)
+    assert batch.latest_probe_count() == sum(m._nprobe for m in members)
+    batch.step(7)
+    got = batch.read_latest_probes()
+    want = np.concatenate([m.probes()[-1] for m in members if m._nprobe])
+    assert np.array_equal(got, want)
+
+
 def test_small_grids_fp32(cuda_device):
     """The band pass on grids with few interior rows (40 x 24: 18 rows between
     the top and bottom layers; 8 x 8: 2)."""
