@@ -14,7 +14,7 @@
  *   Sec. 2.3-2.5               MSD impedance, poles, residues, ADE states
  *   Sec. 3.1  Eqs. ns-rotation, ns-ellipse, ns-poly2d .. ns-readout, ns-ghost
  *   Sec. 3.2                   six coupling steps per RK stage per ghost point
- * Readings where the paper is silent (documented in the design notes):
+ * Readings where the paper is silent:
  *   RK coefficients: 2N-storage Jameson alpha = (1/4, 1/3, 1/2, 1); a classical
  *   Butcher RK4 mode is kept for cross-checks.  The source time factor enters
  *   each stage as the moment of sin(w t) over the step that keeps the scheme
