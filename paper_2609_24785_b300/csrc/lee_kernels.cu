@@ -1048,6 +1048,22 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
+// L2 policy for data read once per stage (the Q^n tile of a stage: no other
+// tile reads it), so that L2 keeps the halo boxes that neighbouring tiles
+// read again (on the sweep: 0.16 GB less DRAM traffic per stage-2 launch)
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void tma_load_3d_hint(void *dst, const void *map, uint64_t *bar, int x, int y, int z,
+                                                 uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z), "l"(policy)
+        : "memory");
+}
 __device__ __forceinline__ void tma_load_3d(void *dst, const void *map, uint64_t *bar, int x, int y, int z) {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::
@@ -1246,7 +1262,8 @@ stencil_ws_kernel(const InstDesc *__restrict__ inst, const int4 *__restrict__ st
                 unsigned char *sb = base + (size_t)b * W::STAGE_BYTES;
                 mbar_arrive_expect_tx(&full[b], stage == 1 ? W::HALO_BYTES : W::STAGE_BYTES);
                 tma_load_3d(sb, d.tmap[inb], &full[b], x0 - HALO, y0 - HALO, 0);
-                if (stage != 1) tma_load_3d(sb + W::HALO_BYTES, d.tmap[3], &full[b], x0, y0, 0);
+                if (stage != 1)
+                    tma_load_3d_hint(sb + W::HALO_BYTES, d.tmap[3], &full[b], x0, y0, 0, policy_evict_first());
             }
             ++issued;
             if (++pr == st.w) { pr = 0; ++pj; }
