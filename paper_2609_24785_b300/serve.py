@@ -73,6 +73,7 @@ class Report:
     chunks: int
     peak_bytes: int
     peak_members: int
+    busy: float = 0.0                # time with a chunk on the GPU (launch -> drained), s
 
     def latencies(self) -> np.ndarray:
         return np.array([r.latency for r in self.requests if r.status == "ok"])
@@ -104,6 +105,12 @@ class Report:
             "mpoint_stage_per_s": self.point_stages / self.makespan / 1e6 if self.makespan > 0 else math.nan,
             "requests_per_s": len(ok) / self.makespan if self.makespan > 0 else math.nan,
             "chunks": self.chunks,
+            # the share of the makespan with a chunk in flight, and the rate
+            # over that time alone (idle gaps, set-up waits and the tail of
+            # the trace excluded)
+            "busy_s": self.busy,
+            "busy_share": self.busy / self.makespan if self.makespan > 0 else math.nan,
+            "mpoint_stage_per_busy_s": self.point_stages / self.busy / 1e6 if self.busy > 0 else math.nan,
             "peak_device_bytes": self.peak_bytes,
             "peak_members": self.peak_members,
         }
@@ -253,7 +260,7 @@ class Server:
         futures = {}
         used = peak = 0
         peak_members = chunks = 0
-        point_stages = 0.0
+        point_stages = busy = 0.0
         t0 = self.clock()
         now = lambda: self.clock() - t0
         pool = cf.ThreadPoolExecutor(max_workers=self.setup_workers) if self.setup_workers > 0 else _InlineExecutor()
@@ -321,6 +328,7 @@ class Server:
                 status = self.be.wait()
                 dt = self.clock() - t_start
                 chunks += 1
+                busy += dt
                 work = 4.0 * n * sum(r.points for r in members)
                 if dt > 0:
                     self.rate = 0.5 * self.rate + 0.5 * work / dt
@@ -349,7 +357,7 @@ class Server:
         arrivals = [r.arrival for r in reqs]
         dones = [r.t_done for r in reqs if not math.isnan(r.t_done)]
         makespan = (max(dones) - min(arrivals)) if reqs and dones else 0.0
-        return Report(reqs, makespan, point_stages, chunks, peak, peak_members)
+        return Report(reqs, makespan, point_stages, chunks, peak, peak_members, busy)
 
 
 def solo_reference(case: workloads.Case, precision: str = "fp32") -> np.ndarray:

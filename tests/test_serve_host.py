@@ -92,6 +92,9 @@ def test_all_requests_complete_with_exact_step_counts():
     s = rep.summary()
     assert s["completed"] == 8 and s["p50_s"] <= s["p99_s"]
     assert s["mpoint_stage_per_s"] > 0
+    # GPU-busy time: inside the makespan, and the busy-time rate is the higher one
+    assert 0 < s["busy_s"] <= s["makespan_s"] and 0 < s["busy_share"] <= 1
+    assert s["mpoint_stage_per_busy_s"] >= s["mpoint_stage_per_s"]
 
 
 def test_late_arrival_joins_a_running_batch():
