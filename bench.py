@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lee", choices=["lee", "reference"])
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "rational", "cylinder", "free", "flat", "monopole"])
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "rational", "trace", "cylinder", "free", "flat", "monopole"])
     ap.add_argument("--count", type=int, default=512)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--sustained-rate", type=float, default=3.0,
                     help="arrival rate of the sustainable serving trace (0: skip)")
     ap.add_argument("--sustained-duration", type=float, default=30.0)
+    ap.add_argument("--serve-chunk-ms", type=float, default=40.0,
+                    help="serving chunk length: members join and leave between chunks")
     return ap.parse_args()
 
 
@@ -93,6 +95,15 @@ def workload_cases(args, rank, accept=None):
                 "{256,384,512,768,1024}, cylinder r = 0.1 n, two real poles + one complex pair "
                 "(4 ADE states per ghost), seed %d" % (args.count, 24785 + rank))
         return cases, rejected, desc
+    if args.workload == "trace":
+        # the serving mix at steady state: the first second of the 200/s trace
+        # as one batch, every request resident from the start
+        trace = workloads.serving_trace(rate=200.0, duration=1.0, seed=24786 + rank, accept=accept)
+        cases = [c for _, c in trace]
+        desc = ("first 1 s of the 200/s serving trace as one static batch: %d instances, n in "
+                "{256,...,2048}, half flat walls (ramp 12, 0.4), half cylinders (ramp 12, 0.04), seed %d"
+                % (len(cases), 24786 + rank))
+        return cases, 0, desc
     if args.workload == "free":
         # diagnostic: no wall, so every tile away from the outer band is interior
         cases = []
@@ -266,11 +277,14 @@ def run_serving(args):
     trace = workloads.serving_trace(rate=args.serve_rate, duration=args.serve_duration, accept=accept)
     out = {"trace": describe(trace, args.serve_rate, args.serve_duration, rejected[0]),
            "budget_bytes": 80 * 10**9}
-    rep = serve.Server(serve.LeeBackend("fp32"), budget_bytes=80 * 10**9).run(trace, realtime=True)
+    rep = serve.Server(serve.LeeBackend("fp32"), budget_bytes=80 * 10**9, chunk_ms=args.serve_chunk_ms).run(
+        trace, realtime=True)
+    out["chunk_ms"] = args.serve_chunk_ms
     out["fp32_batched"] = rep.summary()
     if args.serve_fp64:
         sub = trace[:args.serve_fp64]
-        rep32 = serve.Server(serve.LeeBackend("fp32"), budget_bytes=80 * 10**9).run(sub, realtime=True)
+        rep32 = serve.Server(serve.LeeBackend("fp32"), budget_bytes=80 * 10**9,
+                             chunk_ms=args.serve_chunk_ms).run(sub, realtime=True)
         rep64 = serve.Server(serve.LeeBackend("fp64", batching=False), max_slots=1,
                              budget_bytes=80 * 10**9).run(sub, realtime=True)
         out["subset"] = "first %d requests of the trace, served alone in both modes" % len(sub)
@@ -280,7 +294,8 @@ def run_serving(args):
         rejected[0] = 0
         tr = workloads.serving_trace(rate=args.sustained_rate, duration=args.sustained_duration, seed=24787,
                                      accept=accept)
-        rep = serve.Server(serve.LeeBackend("fp32"), budget_bytes=80 * 10**9).run(tr, realtime=True)
+        rep = serve.Server(serve.LeeBackend("fp32"), budget_bytes=80 * 10**9,
+                           chunk_ms=args.serve_chunk_ms).run(tr, realtime=True)
         out["sustained_trace"] = describe(tr, args.sustained_rate, args.sustained_duration, rejected[0])
         out["sustained_fp32_batched"] = rep.summary()
     return out
