@@ -30,11 +30,18 @@ struct Layout {
 
 // TMA stencil work list of one instance: columns of tiles (instance, tile
 // column, first tile row, tiles), cut into segments of at most `seg` tiles so
-// that small batches still give every SM work
-void append_strips(std::vector<int4> &out, int inst, const InstDesc &d, int seg) {
+// that small batches still give every SM work; inert tiles (all solid, no
+// ghost: their outputs stay zero) are left out
+void append_strips(std::vector<int4> &out, int inst, const InstDesc &d, int seg, const std::vector<uint32_t> &flags) {
+    auto inert = [&](int tx, int ty) { return (flags[(size_t)ty * d.tiles_x + tx] & TILE_INERT) != 0; };
     for (int tx = 0; tx < d.tiles_x; ++tx)
-        for (int ty = 0; ty < d.tiles_y; ty += seg)
-            out.push_back(make_int4(inst, tx, ty, std::min(seg, d.tiles_y - ty)));
+        for (int ty = 0; ty < d.tiles_y;) {
+            if (inert(tx, ty)) { ++ty; continue; }
+            int len = 0;
+            while (ty + len < d.tiles_y && len < seg && !inert(tx, ty + len)) ++len;
+            out.push_back(make_int4(inst, tx, ty, len));
+            ty += len;
+        }
 }
 int strip_segment(long long total_tiles, int strips_per_sm = 2) {
     const long long n = (long long)strips_per_sm * num_sms();
@@ -583,7 +590,7 @@ int lee_bind(lee_ctx *ctx, void *dev_ptr, long long dev_bytes, void *stream) {
     d.use_tma = ctx->kernel_mode == KERNEL_TMA;
     {
         std::vector<int4> strips;
-        append_strips(strips, 0, d, strip_segment((long long)d.tiles_x * d.tiles_y));
+        append_strips(strips, 0, d, strip_segment((long long)d.tiles_x * d.tiles_y), P.tile_flags);
         ctx->nstrips = (int)strips.size();
         CK(cudaMemcpyAsync(ctx->dev + L.strips, strips.data(), strips.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
         CK(cudaStreamSynchronize(s));
@@ -924,7 +931,7 @@ static int batch_refresh(lee_batch *b) {
         tp[i + 1] = tp[i] + descs[i].ntiles;
         band_chunks((int)i, b->members[i]->nband, bch);
         append_chunks(chunks, (int)i, descs[i].ng);
-        append_strips(strips, (int)i, descs[i], seg);
+        append_strips(strips, (int)i, descs[i], seg, b->members[i]->plan.tile_flags);
         total_ghosts += descs[i].ng;
         if (descs[i].np > 0) pi.push_back((int)i);
     }
@@ -956,11 +963,16 @@ static int batch_refresh(lee_batch *b) {
                             if (c->plan.kind[(size_t)y * d.nx + x] != 1) { ok = false; break; }
                     if (ok) { isfar[(size_t)ty * d.tiles_x + tx] = 1; far.push_back(make_int4((int)i, x0, y0, 0)); }
                 }
+            const std::vector<uint32_t> &tf = c->plan.tile_flags;
+            auto skip = [&](int tx, int ty) {
+                const size_t t = (size_t)ty * d.tiles_x + tx;
+                return isfar[t] || (tf[t] & TILE_INERT);
+            };
             for (int tx = 0; tx < d.tiles_x; ++tx)
                 for (int ty = 0; ty < d.tiles_y;) {
-                    if (isfar[(size_t)ty * d.tiles_x + tx]) { ++ty; continue; }
+                    if (skip(tx, ty)) { ++ty; continue; }
                     int len = 0;
-                    while (ty + len < d.tiles_y && !isfar[(size_t)(ty + len) * d.tiles_x + tx] && len < seg) ++len;
+                    while (ty + len < d.tiles_y && !skip(tx, ty + len) && len < seg) ++len;
                     near.push_back(make_int4((int)i, tx, ty, len));
                     ty += len;
                 }

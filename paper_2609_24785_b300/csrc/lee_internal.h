@@ -37,6 +37,8 @@ constexpr uint32_t TILE_BAND = 1u;      // output region meets the 3 outer layer
 constexpr uint32_t TILE_MIXED = 2u;     // has non-fluid or out-of-grid outputs
 constexpr uint32_t TILE_SPONGE = 4u;    // meets the absorbing ramp along the outer edges
 constexpr uint32_t TILE_BAND_FLUID = 8u; // band tile whose band nodes and their 7-node windows are all fluid
+constexpr uint32_t TILE_INERT = 32u;    // every node solid, none a ghost: never read by a fluid node's
+                                        // stencil, stays zero in every buffer, so no kernel visits it
 
 // Opt-in absorbing ramp along the non-periodic edges (lee_set_sponge; off by
 // default, as in the paper): damping rate (kappa / h) ((W - d) / W)^2 at a

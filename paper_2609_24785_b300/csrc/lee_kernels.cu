@@ -937,6 +937,7 @@ stencil_kernel(const InstDesc *__restrict__ inst, int ninst, const int *__restri
         const int tx = lt % d.tiles_x, ty = lt / d.tiles_x;
         const int xt = tx * TILE_X, yt = ty * TILE_Y;
         const uint32_t flags = __ldg(d.tile_flags + lt);
+        if (flags & TILE_INERT) continue;      // all solid, no ghost: outputs stay zero (whole block)
         const T *qin = (const T *)d.q[inb];
         const long long plane = d.plane;
         const int pitch = d.pitch, nx = d.nx, ny = d.ny;

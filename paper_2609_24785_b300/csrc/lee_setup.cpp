@@ -497,6 +497,10 @@ int build_plan(int nx, int ny, double h, double x0, double y0, int per_x, int pe
                     }
                 if (fluid) f |= TILE_BAND_FLUID;
             }
+            bool inert = true;                 // solid (kind 0) everywhere: no fluid node, no ghost
+            for (int j = ya; j < std::min(yb, ny) && inert; ++j)
+                for (int i = xa; i < std::min(xb, nx) && inert; ++i) inert = P.kind[(size_t)j * nx + i] == 0;
+            if (inert) f |= TILE_INERT;
             P.tile_flags[(size_t)ty * P.tiles_x + tx] = f;
         }
     return LEE_OK;
