@@ -30,18 +30,19 @@ struct Layout {
 
 // TMA stencil work list of one instance: columns of tiles (instance, tile
 // column, first tile row, tiles), cut into segments of at most `seg` tiles so
-// that small batches still give every SM work; inert tiles (all solid, no
-// ghost: their outputs stay zero) are left out
+// that small batches still give every SM work.  Inert tiles (all solid, no
+// ghost: their outputs stay zero) at either end of a column are left out (the
+// solid side of a straight wall: about half the tiles); inert tiles between
+// live ones stay, so that a column is never split (on the cylinder sweep,
+// splitting around the few tiles inside the cylinders cost 1.2 %).
 void append_strips(std::vector<int4> &out, int inst, const InstDesc &d, int seg, const std::vector<uint32_t> &flags) {
     auto inert = [&](int tx, int ty) { return (flags[(size_t)ty * d.tiles_x + tx] & TILE_INERT) != 0; };
-    for (int tx = 0; tx < d.tiles_x; ++tx)
-        for (int ty = 0; ty < d.tiles_y;) {
-            if (inert(tx, ty)) { ++ty; continue; }
-            int len = 0;
-            while (ty + len < d.tiles_y && len < seg && !inert(tx, ty + len)) ++len;
-            out.push_back(make_int4(inst, tx, ty, len));
-            ty += len;
-        }
+    for (int tx = 0; tx < d.tiles_x; ++tx) {
+        int lo = 0, hi = d.tiles_y;
+        while (lo < hi && inert(tx, lo)) ++lo;
+        while (hi > lo && inert(tx, hi - 1)) --hi;
+        for (int ty = lo; ty < hi; ty += seg) out.push_back(make_int4(inst, tx, ty, std::min(seg, hi - ty)));
+    }
 }
 int strip_segment(long long total_tiles, int strips_per_sm = 2) {
     const long long n = (long long)strips_per_sm * num_sms();
