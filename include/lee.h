@@ -198,6 +198,15 @@ int lee_sync(lee_ctx *ctx);
 int lee_read_field(lee_ctx *ctx, int which, double *host);
 /* Node kinds, nx*ny bytes: 0 solid, 1 fluid, 2 ghost. */
 int lee_read_mask(lee_ctx *ctx, unsigned char *host);
+/* Stencil tile classes after lee_plan (host arrays; test hook): *tiles_x and
+ * *tiles_y receive the tile grid of the plan's tile shape and, when host is
+ * not NULL, host receives tiles_x*tiles_y flag words, row-major: bit 0 the
+ * tile's outputs meet the three outer layers (band), bit 1 some output is
+ * not fluid or lies past the grid, bit 2 the tile meets the absorbing ramp,
+ * bit 3 every band node of the tile and every node of its 7-node windows is
+ * fluid, bit 5 every node is solid and none is a ghost (inert: no kernel
+ * visits it at the ends of a tile column, its values stay zero). */
+int lee_tile_flags(lee_ctx *ctx, unsigned int *host, int *tiles_x, int *tiles_y);
 /* ADE states X^n, n_ghost x n_states doubles, in the ghost order of lee_ghost_info. */
 int lee_read_ade(lee_ctx *ctx, double *host);
 /* Completed time steps. */

@@ -692,6 +692,15 @@ int lee_read_mask(lee_ctx *ctx, unsigned char *host) {
     return LEE_OK;
 }
 
+int lee_tile_flags(lee_ctx *ctx, unsigned int *host, int *tiles_x, int *tiles_y) {
+    if (!ctx || !tiles_x || !tiles_y) return LEE_ERR_ARG;
+    if (!ctx->planned) return fail(ctx, LEE_ERR_ARG, "not planned");
+    *tiles_x = ctx->plan.tiles_x;
+    *tiles_y = ctx->plan.tiles_y;
+    if (host) std::memcpy(host, ctx->plan.tile_flags.data(), ctx->plan.tile_flags.size() * sizeof(unsigned int));
+    return LEE_OK;
+}
+
 int lee_read_ade(lee_ctx *ctx, double *host) {
     if (!ctx || !host) return LEE_ERR_ARG;
     if (!ctx->bound) return fail(ctx, LEE_ERR_ARG, "not bound");

@@ -81,6 +81,7 @@ SIGNATURES = {
     "lee_sync": (C.c_int, [_vp]),
     "lee_read_field": (C.c_int, [_vp, C.c_int, _dp]),
     "lee_read_mask": (C.c_int, [_vp, C.POINTER(C.c_ubyte)]),
+    "lee_tile_flags": (C.c_int, [_vp, C.POINTER(C.c_uint), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "lee_read_ade": (C.c_int, [_vp, _dp]),
     "lee_get_step": (C.c_int, [_vp, _llp]),
     "lee_energy": (C.c_int, [_vp, _dp]),
@@ -264,6 +265,15 @@ class Solver:
         out = np.empty(self.nx * self.ny, dtype=np.uint8)
         self._c(self.L.lee_read_mask(self.ctx, out.ctypes.data_as(C.POINTER(C.c_ubyte))))
         return out.reshape(self.ny, self.nx)
+
+    def tile_flags(self):
+        """Stencil tile classes of the plan (tiles_y x tiles_x flag words; bits
+        in include/lee.h, lee_tile_flags)."""
+        tx, ty = C.c_int(), C.c_int()
+        self._c(self.L.lee_tile_flags(self.ctx, None, C.byref(tx), C.byref(ty)))
+        out = np.zeros(max(tx.value * ty.value, 1), dtype=np.uint32)
+        self._c(self.L.lee_tile_flags(self.ctx, out.ctypes.data_as(C.POINTER(C.c_uint)), C.byref(tx), C.byref(ty)))
+        return out[:tx.value * ty.value].reshape(ty.value, tx.value)
 
     def ade(self):
         ng, ns = self.sizes.n_ghost, self.sizes.n_states

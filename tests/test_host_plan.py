@@ -152,6 +152,47 @@ def test_tile_shape_selection():
         sp.set_tile(128, 28)
 
 
+@pytest.mark.parametrize("wall", [("line", 30.0), ("line", 75.0), ("cyl", 0.12)], ids=["line30", "line75", "cyl"])
+def test_tile_flags_follow_the_mask(wall):
+    """lee_tile_flags: every class bit of every 64 x 40 tile of a ragged
+    200 x 136 grid (ramp of 12 layers) restated from the node kinds and the
+    tile's rectangle: band (meets the three outer layers), mixed (a non-fluid
+    or out-of-grid output), ramp, band windows all fluid, inert (every node
+    solid and none a ghost)."""
+    h = workloads.H
+    nx, ny, W = 200, 136, 12
+    cx, cy = (nx - 1) / 2 * h, (ny - 1) / 2 * h
+    geo = ("line", cx + 0.37 * h, cy, math.radians(wall[1])) if wall[0] == "line" else ("cyl", cx, cy, wall[1] * nx * h)
+    case = workloads.Case("flags", nx, ny, wall=geo, imp=("msd", 1.0, 0.05, 5.0), sponge=(W, 0.04))
+    s = lee.Solver(nx, ny, h, case.cfl, precision="fp32")
+    workloads.apply_to(case, s)
+    s.set_tile(64, 40)
+    s.plan()
+    kind = s.mask()
+    got = s.tile_flags()
+    assert got.shape == (-(-ny // 40), -(-nx // 64))
+    assert (got & 32).any() or wall[0] == "cyl"          # straight walls leave whole tiles solid
+    for ty in range(got.shape[0]):
+        for tx in range(got.shape[1]):
+            xa, ya = 64 * tx, 40 * ty
+            xb, yb = xa + 64, ya + 40
+            k = kind[ya:min(yb, ny), xa:min(xb, nx)]
+            band = xa < 3 or xb > nx - 3 or ya < 3 or yb > ny - 3
+            f = (1 if band else 0) | (2 if (xb > nx or yb > ny or (k != 1).any()) else 0)
+            f |= 4 if (xa < W or xb > nx - W or ya < W or yb > ny - W) else 0
+            if band:
+                ok = True
+                for j in range(ya, min(yb, ny)):
+                    for i in range(xa, min(xb, nx)):
+                        if not (j < 3 or j > ny - 4 or i < 3 or i > nx - 4):
+                            continue
+                        sx, sy = min(max(i - 3, 0), nx - 7), min(max(j - 3, 0), ny - 7)
+                        ok = ok and (kind[j, sx:sx + 7] == 1).all() and (kind[sy:sy + 7, i] == 1).all()
+                f |= 8 if ok else 0
+            f |= 32 if (k == 0).all() else 0
+            assert int(got[ty, tx]) == f, (tx, ty, int(got[ty, tx]), f)
+
+
 def test_autotune_sample_is_size_stratified():
     from paper_2609_24785_b300 import autotune
     cases, _ = workloads.sweep(60, seed=7)
