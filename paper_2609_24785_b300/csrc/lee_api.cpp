@@ -542,7 +542,7 @@ int lee_bind(lee_ctx *ctx, void *dev_ptr, long long dev_bytes, void *stream) {
     // [0..1] tile prefix, [2..3] ghost prefix, [4] probe instance
     ctx->nband = ctx_band_nodes(ctx);
     std::vector<int4> bch;
-    band_chunks(0, ctx->nband, bch);
+    band_chunks(0, ctx->nband, bch, P.kind.data(), P.nx, P.ny);
     ctx->nbchunks = (int)bch.size();
     if (!bch.empty())
         CK(cudaMemcpyAsync(ctx->dev + L.bchunks, bch.data(), bch.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
@@ -939,7 +939,8 @@ static int batch_refresh(lee_batch *b) {
     for (size_t i = 0; i < n; ++i) {
         descs[i] = b->members[i]->hd;
         tp[i + 1] = tp[i] + descs[i].ntiles;
-        band_chunks((int)i, b->members[i]->nband, bch);
+        band_chunks((int)i, b->members[i]->nband, bch, b->members[i]->plan.kind.data(), b->members[i]->plan.nx,
+                    b->members[i]->plan.ny);
         append_chunks(chunks, (int)i, descs[i].ng);
         append_strips(strips, (int)i, descs[i], seg, b->members[i]->plan.tile_flags);
         total_ghosts += descs[i].ng;

@@ -221,7 +221,8 @@ bool uses_band_pass(int precision, int kernel_mode, int tile_w, int tile_h);
 int default_band_tile_stages();         // BatchView::band_tile unless a batch sets its own
 bool tma_tile_supported(int tw, int th);
 int band_nodes(int nx, int ny, int per_x, int per_y);
-void band_chunks(int inst, int nband, std::vector<int4> &out);
+// band_kernel work list of one instance (kind: its node kinds, host order)
+void band_chunks(int inst, int nband, std::vector<int4> &out, const uint8_t *kind, int nx, int ny);
 long long launch_count();
 void count_launch(int n = 1);
 // message for lee_last_error(NULL) (entry points without a context)

@@ -1431,8 +1431,24 @@ int band_nodes(int nx, int ny, int per_x, int per_y) {
 
 // band_kernel work list of one instance: chunks of BAND_CHUNK band nodes,
 // (instance, first band node, count, 0), one per block iteration
-void band_chunks(int inst, int nband, std::vector<int4> &out) {
-    for (int f = 0; f < nband; f += BAND_CHUNK) out.push_back(make_int4(inst, f, std::min(BAND_CHUNK, nband - f), 0));
+// (chunks whose nodes are all non-fluid, e.g. on the solid side of a straight
+// wall, are left out: the kernel would skip each of their nodes)
+void band_chunks(int inst, int nband, std::vector<int4> &out, const uint8_t *kind, int nx, int ny) {
+    auto node = [&](int b, int &gx, int &gy) {
+        if (b < 3 * nx) { gy = b / nx; gx = b % nx; }
+        else if (b < 6 * nx) { b -= 3 * nx; gy = ny - 3 + b / nx; gx = b % nx; }
+        else { b -= 6 * nx; const int r = b / 6, c = b - 6 * r; gy = 3 + r; gx = c < 3 ? c : nx - 6 + c; }
+    };
+    for (int f = 0; f < nband; f += BAND_CHUNK) {
+        const int cnt = std::min(BAND_CHUNK, nband - f);
+        bool any = kind == nullptr;
+        for (int b = f; b < f + cnt && !any; ++b) {
+            int gx, gy;
+            node(b, gx, gy);
+            any = kind[(size_t)gy * nx + gx] == 1;
+        }
+        if (any) out.push_back(make_int4(inst, f, cnt, 0));
+    }
 }
 
 // After the warp-specialised stencil of a stage: every fluid node of the three
