@@ -118,6 +118,29 @@ def test_argument_errors():
         s2.step(1)                               # not bound
 
 
+def test_batch_argument_errors():
+    """Batch entry points reject bad arguments before any device work: band
+    stage masks outside stages 2-4, missing outputs, an unbound batch."""
+    L = lee.load()
+    b = C.c_void_p()
+    assert L.lee_batch_create(C.byref(b), 7) == lee.LEE_ERR_ARG
+    assert L.lee_batch_create(C.byref(b), lee.LEE_FP32) == lee.LEE_OK
+    try:
+        for bad in (1, 2, 32, 64, -2):          # bit 1 = stage 1, bits past stage 4, below -1
+            assert L.lee_batch_set_band_in_tile(b, bad) == lee.LEE_ERR_ARG
+        for good in (0, 4, 28, -1):
+            assert L.lee_batch_set_band_in_tile(b, good) == lee.LEE_OK
+        m = C.c_int()
+        assert L.lee_batch_band_in_tile(b, None) == lee.LEE_ERR_ARG
+        assert L.lee_batch_band_in_tile(b, C.byref(m)) == lee.LEE_OK and m.value in (0, 4, 8, 12, 16, 20, 24, 28)
+        n = C.c_longlong()
+        assert L.lee_batch_read_latest_probes_async(b, None, None) == lee.LEE_ERR_ARG
+        assert L.lee_batch_read_latest_probes_async(b, None, C.byref(n)) == lee.LEE_ERR_ARG   # not bound
+        assert L.lee_batch_step(b, 1) == lee.LEE_ERR_ARG                                         # not bound
+    finally:
+        L.lee_batch_destroy(b)
+
+
 def test_probe_stencils_match_oracle():
     case = workloads.cylinder_pulse(256)
     s = make_solver(case, bind=False)
