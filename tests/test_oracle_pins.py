@@ -808,3 +808,38 @@ def test_ade_wall_velocity_matches_the_fluid():
     assert e2 < 5e-3, (e1, e2)
     assert e1 / e2 > 8.0, (e1, e2)
     assert _wall_velocity_consistency(128, sign=-1.0) > 0.5
+
+
+# ------------------------------------------------------------------ cloud shape (Sec. 3.1, Eq. ns-ellipse)
+@pytest.mark.parametrize("geom", ["cyl", 0, 30, 72])
+def test_cloud_is_the_fluid_nodes_of_the_ellipse(geom):
+    """Each ghost's cloud is exactly the set of fluid nodes (not ghost, not
+    solid) inside the ellipse (x'/R_n)^2 + (y'/R_t)^2 <= 1 about its boundary
+    point, x' along the wall normal and y' along the wall, in cells, with
+    R_n = 8 and R_t = 3 (tests/golden/paper_constants.txt: R_n = 2k, R_t =
+    k/2 + 1, k = 4), brute force over every node of the box.  Swapping the
+    axes or the radii changes the sets."""
+    gold = {}
+    for line in open(__file__.replace("test_oracle_pins.py", "golden/paper_constants.txt")):
+        if line.strip() and not line.startswith("#"):
+            gold[line.split("=")[0].strip()] = float(line.split("=")[1].split("#")[0].strip())
+    Rn, Rt = gold["Rn"], gold["Rt"]
+    o = (_cyl(48, 9.3) if geom == "cyl" else _line(48, geom)).setup()
+    X, Y = _nodes(o)
+    kind = o.kind().reshape(-1)
+    xs, ys = X.reshape(-1), Y.reshape(-1)
+
+    def ellipse(G, a, b):
+        n = G["n"]
+        t = np.array([-n[1], n[0]])
+        dx, dy = (xs - G["bp"][0]) / o.h, (ys - G["bp"][1]) / o.h
+        xp, yp = n[0] * dx + n[1] * dy, t[0] * dx + t[1] * dy
+        return set(np.nonzero((kind == 1) & ((xp / a) ** 2 + (yp / b) ** 2 <= 1.0))[0].tolist())
+
+    swapped_differs = False
+    for g in range(o.n_ghost):
+        G = o.ghost(g)
+        cloud = set(G["cloud"].tolist())
+        assert cloud == ellipse(G, Rn, Rt), g
+        swapped_differs = swapped_differs or cloud != ellipse(G, Rt, Rn)
+    assert swapped_differs
