@@ -350,6 +350,33 @@ def test_lagrange_factor_closed_forms():
 
 
 # ------------------------------------------------------------------ P5
+def test_stage_forcing_keeps_fourth_order():
+    """Reading R2 (source stage times, Secs. 2.2 and 4.3): the four-stage
+    low-storage scheme with the oracle's stage forcing (orc_stage_forcing)
+    integrates y' = lambda y + sin(w t) at 4th order against the closed-form
+    solution; sampling sin at t_n + alpha_{k-1} dt instead drops to 2nd."""
+    lam, w, y0, T = -2.0, 3.0, 1.0, 2.0
+    a, b = -lam / (lam ** 2 + w ** 2), -w / (lam ** 2 + w ** 2)
+    exact = (y0 - b) * math.exp(lam * T) + a * math.sin(w * T) + b * math.cos(w * T)
+    alpha = (0.25, 1 / 3, 0.5, 1.0)
+
+    def run(dt, sampled):
+        y = y0
+        for i in range(int(round(T / dt))):
+            tn, yk = i * dt, y
+            for k in range(1, 5):
+                s = (math.sin(w * (tn + (alpha[k - 2] if k > 1 else 0.0) * dt)) if sampled
+                     else oracle.stage_forcing(w, tn, dt, k))
+                yk = y + alpha[k - 1] * dt * (lam * yk + s)
+            y = yk
+        return abs(y - exact)
+
+    e = [run(dt, False) for dt in (0.04, 0.02, 0.01)]
+    assert all(3.8 < math.log2(e[i] / e[i + 1]) < 4.3 for i in range(2)), e
+    s = [run(dt, True) for dt in (0.04, 0.02, 0.01)]
+    assert all(1.8 < math.log2(s[i] / s[i + 1]) < 2.2 for i in range(2)), s
+
+
 def test_low_storage_equals_classical_rk4_without_source():
     """F5: for the linear, autonomous semi-discrete system (fields + ghost fill
     + ADE + radiation band) the 2N-storage alpha = (1/4,1/3,1/2,1) scheme and
