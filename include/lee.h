@@ -205,7 +205,9 @@ int lee_read_mask(lee_ctx *ctx, unsigned char *host);
  * not fluid or lies past the grid, bit 2 the tile meets the absorbing ramp,
  * bit 3 every band node of the tile and every node of its 7-node windows is
  * fluid, bit 5 every node is solid and none is a ghost (inert: no kernel
- * visits it at the ends of a tile column, its values stay zero). */
+ * visits it at the ends of a tile column, its values stay zero).  Sec. 3.1
+ * defines the node kinds the classes follow.  LEE_ERR_ARG for a NULL context
+ * or tile-count pointer, or before lee_plan; host is caller-owned. */
 int lee_tile_flags(lee_ctx *ctx, unsigned int *host, int *tiles_x, int *tiles_y);
 /* ADE states X^n, n_ghost x n_states doubles, in the ghost order of lee_ghost_info. */
 int lee_read_ade(lee_ctx *ctx, double *host);
@@ -299,7 +301,8 @@ int lee_batch_set_stage_fusion(lee_batch *b, int on);
  * bit mask, overrides it).  LEE_ERR_ARG for bits outside 2..4.  At a step
  * boundary; no effect on other kernels. */
 int lee_batch_set_band_in_tile(lee_batch *b, int stage_mask);
-/* The stage mask in effect (see lee_batch_set_band_in_tile). */
+/* The stage mask in effect (see lee_batch_set_band_in_tile); LEE_ERR_ARG for
+ * a NULL argument. */
 int lee_batch_band_in_tile(lee_batch *b, int *stage_mask);
 /* Tiles that the fused pass covers and the batch's total tiles (after the
  * members are final; refreshes the batch's tables). */
@@ -309,7 +312,8 @@ int lee_batch_fused_tiles(lee_batch *b, long long *fused, long long *total);
  * each member's probes in its lee_set_probes order, written to host (count
  * doubles; pinned memory keeps the copy asynchronous) by one gather kernel and
  * one copy on the batch stream: it is complete after the stream drains.
- * host = NULL returns the count only. */
+ * host = NULL returns the count only.  LEE_ERR_ARG for a NULL batch or count
+ * or an unbound batch, LEE_ERR_CUDA if the launch or copy fails. */
 int lee_batch_read_latest_probes_async(lee_batch *b, double *host, long long *count);
 /* Name of the stencil kernel variant the batch launches (static string; ""
  * before lee_batch_bind or without members). */
