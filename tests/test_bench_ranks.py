@@ -45,3 +45,27 @@ def test_replicas_aggregate_over_two_gloo_ranks():
     assert c0 != c1                              # independent instances per rank
     assert "seed 24785" in d0 and "seed 24786" in d1
     assert sorted(set(x[0] for x in c0)) <= [256, 384, 512, 768, 1024]
+
+
+def _reference_arm(env_rank):
+    import json
+    import subprocess
+    env = dict(os.environ, RANK=str(env_rank), LOCAL_RANK=str(env_rank), WORLD_SIZE="2", OMP_NUM_THREADS="2")
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "2", "--warmup", "1"], env=env, capture_output=True, text=True, timeout=300)
+    lines = [json.loads(l) for l in p.stdout.splitlines() if l.startswith("{")]
+    return p.returncode, lines
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    """bench.py --impl reference under torchrun: rank 0 times the oracle and
+    prints the one JSON line (impl, cpu_baseline, e2e of the line's own
+    metric); the other ranks exit 0 without work."""
+    rc1, lines1 = _reference_arm(1)
+    assert rc1 == 0 and lines1 == []
+    rc0, lines0 = _reference_arm(0)
+    assert rc0 == 0 and len(lines0) == 1
+    line = lines0[0]
+    assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
