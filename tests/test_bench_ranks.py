@@ -1,7 +1,7 @@
 """Host logic of bench.py's multi-GPU path (replicas): two gloo ranks on the
 CPU.  Each rank draws its own sweep (seed 24785 + rank) of the same size and
 size mix, and the job's figures are the slowest rank's time and the sum of
-the ranks' fluid nodes."""
+the ranks' fluid nodes; the reference arm runs on rank 0 alone."""
 import os
 import sys
 import types
